@@ -1,0 +1,127 @@
+/*
+ * dfc_lrr.h -- C ABI of the GB300 (sm_103a) DFC-LRR solver.
+ *
+ * Problem (eq. (1), Section 1; eq. (2), Section 2.2):
+ *   LRR       min ||Z||_* + lambda ||S||_{2,1}   s.t.  M = M Z + S
+ *   block i   min ||Z_i||_* + lambda ||S_i||_{2,1} s.t. C_i = M Z_i + S_i
+ * with ||.||_* the nuclear norm and ||.||_{2,1} the sum of column 2-norms.
+ * DFC-LRR (Algorithm 1, Section 2.2): D step = random column partition of M
+ * into t blocks C_i (passed in as `perm` + `offsets`); F step = the t block
+ * problems, each solved by the inexact augmented-Lagrangian iteration named as
+ * the base solver in Section 4; C step = column projection of
+ * [Z_1 ... Z_t] onto the column space of Z_1.
+ *
+ * Memory: every array argument marked (device) is a device pointer that the
+ * caller allocates and owns; (host) arrays are ordinary host memory.  Matrices
+ * are column-major.  The library never frees caller memory.  Work memory is a
+ * single caller-provided device buffer of at least lrr_workspace_bytes() bytes
+ * (256-byte aligned); with workspace == NULL the library allocates it with
+ * cudaMallocAsync on `stream` and frees it before returning.
+ *
+ * Streams: all device work is queued on `stream`; the call returns after the
+ * stream has drained the solve (it reads convergence flags and the per-block
+ * counters back to the host).
+ *
+ * Errors: every entry point returns an lrr_status.  Negative values are
+ * failures (nothing in `result` is valid); LRR_NOT_CONVERGED (> 0) means all
+ * outputs are written but at least one block stopped at max_iter.  No entry
+ * point aborts, traps or prints.
+ */
+#ifndef DFC_LRR_H
+#define DFC_LRR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LRR_API __attribute__((visibility("default")))
+#else
+#define LRR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LRR_OK = 0,
+    LRR_NOT_CONVERGED = 1,      /* outputs valid, some block hit max_iter            */
+    LRR_ERR_INVALID = -1,       /* bad size, pointer, option or partition            */
+    LRR_ERR_NONFINITE = -2,     /* M holds NaN or Inf                                */
+    LRR_ERR_CUDA = -3,          /* a CUDA runtime call failed                        */
+    LRR_ERR_WORKSPACE = -4,     /* workspace too small or misaligned                 */
+    LRR_ERR_RANK = -5,          /* M is numerically zero                             */
+    LRR_ERR_UNSUPPORTED = -6    /* option combination not built (see lrr_status_string) */
+} lrr_status;
+
+typedef enum {
+    LRR_PREC_F64 = 0,    /* every step in float64                                     */
+    LRR_PREC_F32 = 1,    /* iteration in float32, one-time factor in float64          */
+    LRR_PREC_MIXED = 2   /* bf16 tensor-core products with float32 accumulation in the
+                            iteration bulk, float32 refinement phase to convergence    */
+} lrr_precision;
+
+typedef struct {
+    const void* M;              /* (device) m x n, column-major, leading dim ldm >= m;
+                                   float for F32/MIXED, double for F64                  */
+    int64_t m, n, ldm;
+    int32_t t;                  /* number of column blocks, 1 <= t <= n                  */
+    const int64_t* perm;        /* (host) n: block i observes the original columns
+                                   perm[offsets[i] .. offsets[i+1]-1]; a permutation      */
+    const int64_t* offsets;     /* (host) t+1, offsets[0] = 0, offsets[t] = n, strictly
+                                   increasing                                             */
+} lrr_problem;
+
+typedef struct {
+    double lambda;              /* > 0                                                   */
+    double rho;                 /* penalty growth, > 1 (1.1)                             */
+    double mu0;                 /* initial penalty, > 0 (1e-6)                           */
+    double mu_max;              /* penalty cap (1e10)                                    */
+    double eps;                 /* stop when ||C-MZ-S||_inf < eps and ||Z-J||_inf < eps  */
+    int32_t max_iter;           /* >= 1 (1000)                                           */
+    int32_t precision;          /* lrr_precision                                         */
+    int32_t batched;            /* 1: all blocks advance together in every launch;
+                                   0: blocks are solved one after another                */
+    int32_t jacobi_sweeps;      /* max Jacobi sweeps per SVT (0 -> default 8)            */
+    double rank_tol;            /* rank(M) = #{sigma > rank_tol * sigma_max} (0 -> 1e-6)  */
+    double mixed_switch;        /* MIXED: leave bf16 once the primal residual is below
+                                   this (0 -> 1e-3)                                      */
+} lrr_options;
+
+typedef struct {
+    void* Z;                    /* (device, may be NULL) n x n, ld n, original column
+                                   order: the combined estimate (Algorithm 1 output)      */
+    void* S;                    /* (device, may be NULL) m x n, ld m, original order      */
+    int32_t* iters;             /* (host, may be NULL) t: ALM iterations per block        */
+    double* resid;              /* (host, may be NULL) t x 2: final ||C_i-MZ_i-S_i||_inf,
+                                   ||Z_i-J_i||_inf per block                              */
+    int32_t* ranks;             /* (host, may be NULL) t+2: [rank(M), k1, SVT rank of each
+                                   block at its final iteration]                          */
+    double* timings_ms;         /* (host, may be NULL) 3: setup, iteration, combine        */
+} lrr_result;
+
+/* Bytes of device workspace a solve of `p` with options `o` needs (0 on invalid
+ * arguments). */
+LRR_API size_t lrr_workspace_bytes(const lrr_problem* p, const lrr_options* o);
+
+/* Plain LRR, eq. (1): requires p->t == 1 (the one block is all of M, in the
+ * order given by perm).  No C step.  Returns an lrr_status. */
+LRR_API int lrr_solve(const lrr_problem* p, const lrr_options* o, void* workspace, size_t workspace_bytes,
+              lrr_result* r, void* stream);
+
+/* DFC-LRR, Algorithm 1: the t block problems of eq. (2) (F step), then the
+ * column projection onto the column space of Z_1 (C step; skipped for t == 1,
+ * where it is the identity).  Returns an lrr_status. */
+LRR_API int dfc_lrr_solve(const lrr_problem* p, const lrr_options* o, void* workspace, size_t workspace_bytes,
+                  lrr_result* r, void* stream);
+
+/* Fill `o` with the defaults above (lambda = 0.1). */
+LRR_API void lrr_default_options(lrr_options* o);
+
+/* Static description of a status code. */
+LRR_API const char* lrr_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DFC_LRR_H */

@@ -1,0 +1,177 @@
+"""ctypes binding of libdfc_lrr.so (declared in include/dfc_lrr.h).
+
+Argument marshalling only: torch tensors become device pointers, the current
+torch stream becomes the library's stream, and the workspace is a torch
+allocation.  Every step of the solve runs in the library's CUDA kernels; if
+the library is missing or cannot load, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdfc_lrr.so")
+
+LRR_OK, LRR_NOT_CONVERGED = 0, 1
+LRR_PREC_F64, LRR_PREC_F32, LRR_PREC_MIXED = 0, 1, 2
+PRECISIONS = {"f64": LRR_PREC_F64, "f32": LRR_PREC_F32, "mixed": LRR_PREC_MIXED}
+
+# every symbol include/dfc_lrr.h declares
+EXPORTS = ("lrr_workspace_bytes", "lrr_solve", "dfc_lrr_solve", "lrr_default_options", "lrr_status_string")
+
+
+class LrrProblem(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("ldm", ctypes.c_int64),
+                ("t", ctypes.c_int32), ("perm", ctypes.POINTER(ctypes.c_int64)),
+                ("offsets", ctypes.POINTER(ctypes.c_int64))]
+
+
+class LrrOptions(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("rho", ctypes.c_double), ("mu0", ctypes.c_double),
+                ("mu_max", ctypes.c_double), ("eps", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("batched", ctypes.c_int32), ("jacobi_sweeps", ctypes.c_int32),
+                ("rank_tol", ctypes.c_double), ("mixed_switch", ctypes.c_double)]
+
+
+class LrrResult(ctypes.Structure):
+    _fields_ = [("Z", ctypes.c_void_p), ("S", ctypes.c_void_p), ("iters", ctypes.POINTER(ctypes.c_int32)),
+                ("resid", ctypes.POINTER(ctypes.c_double)), ("ranks", ctypes.POINTER(ctypes.c_int32)),
+                ("timings_ms", ctypes.POINTER(ctypes.c_double))]
+
+
+_LIB = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the library (raises OSError if it is not built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise OSError(f"{path} is not built; run paper_1304_5583_gb300/build.py")
+    lib = ctypes.CDLL(path)
+    lib.lrr_workspace_bytes.restype = ctypes.c_size_t
+    lib.lrr_workspace_bytes.argtypes = [ctypes.POINTER(LrrProblem), ctypes.POINTER(LrrOptions)]
+    for fn in (lib.lrr_solve, lib.dfc_lrr_solve):
+        fn.restype = ctypes.c_int
+        fn.argtypes = [ctypes.POINTER(LrrProblem), ctypes.POINTER(LrrOptions), ctypes.c_void_p, ctypes.c_size_t,
+                       ctypes.POINTER(LrrResult), ctypes.c_void_p]
+    lib.lrr_default_options.restype = None
+    lib.lrr_default_options.argtypes = [ctypes.POINTER(LrrOptions)]
+    lib.lrr_status_string.restype = ctypes.c_char_p
+    lib.lrr_status_string.argtypes = [ctypes.c_int]
+    _LIB = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    return load().lrr_status_string(int(code)).decode()
+
+
+class LrrError(RuntimeError):
+    def __init__(self, code: int):
+        super().__init__(f"lrr status {code}: {status_string(code)}")
+        self.code = code
+
+
+@dataclass
+class SolveResult:
+    Z: object            # torch (n, n), column-major storage, original column order
+    S: object            # torch (m, n)
+    iters: np.ndarray    # (t,)
+    resid: np.ndarray    # (t, 2)
+    rank_M: int
+    k1: int
+    block_ranks: np.ndarray
+    timings_ms: np.ndarray
+    status: int
+
+
+def column_major(x):
+    """(rows, cols) tensor with unit row stride (a column-major matrix); copies if needed."""
+    if x.dim() == 2 and x.stride(0) == 1 and x.stride(1) >= max(1, x.shape[0]):
+        return x
+    return x.t().contiguous().t()
+
+
+def options(lam: float, rho: float = 1.1, mu0: float = 1e-6, mu_max: float = 1e10, eps: float = 1e-6,
+            max_iter: int = 1000, precision: str = "f32", batched: bool = True, jacobi_sweeps: int = 0,
+            rank_tol: float = 0.0, mixed_switch: float = 0.0) -> LrrOptions:
+    o = LrrOptions()
+    load().lrr_default_options(ctypes.byref(o))
+    o.lambda_, o.rho, o.mu0, o.mu_max, o.eps = lam, rho, mu0, mu_max, eps
+    o.max_iter, o.precision, o.batched = int(max_iter), PRECISIONS[precision], int(bool(batched))
+    o.jacobi_sweeps, o.rank_tol, o.mixed_switch = int(jacobi_sweeps), float(rank_tol), float(mixed_switch)
+    return o
+
+
+def _problem(M, perm, offsets):
+    perm = np.ascontiguousarray(perm, dtype=np.int64)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    p = LrrProblem()
+    p.M = ctypes.c_void_p(M.data_ptr())
+    p.m, p.n, p.ldm = M.shape[0], M.shape[1], M.stride(1)
+    p.t = len(offsets) - 1
+    p.perm = perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    p.offsets = offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    return p, (perm, offsets)
+
+
+def workspace_bytes(M, perm, offsets, opts: LrrOptions) -> int:
+    p, keep = _problem(M, perm, offsets)
+    return int(load().lrr_workspace_bytes(ctypes.byref(p), ctypes.byref(opts)))
+
+
+def _solve(entry: str, M, perm, offsets, opts: LrrOptions, want_Z=True, want_S=True, workspace=None,
+           raise_on_error=True) -> SolveResult:
+    import torch
+    lib = load()
+    if not M.is_cuda:
+        raise ValueError("M must be a CUDA tensor")
+    M = column_major(M)
+    m, n = M.shape
+    p, keep = _problem(M, perm, offsets)
+    t = p.t
+    need = int(lib.lrr_workspace_bytes(ctypes.byref(p), ctypes.byref(opts)))
+    if need == 0:
+        if raise_on_error:
+            raise LrrError(-1)
+        return SolveResult(Z=None, S=None, iters=np.zeros(t, np.int32), resid=np.zeros((t, 2)), rank_M=0, k1=0,
+                           block_ranks=np.zeros(t, np.int32), timings_ms=np.zeros(3), status=-1)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=M.device)
+    Z = torch.empty((n, n), dtype=M.dtype, device=M.device).t() if want_Z else None
+    S = torch.empty((n, m), dtype=M.dtype, device=M.device).t() if want_S else None
+    iters = np.zeros(t, np.int32)
+    resid = np.zeros((t, 2), np.float64)
+    ranks = np.zeros(t + 2, np.int32)
+    tim = np.zeros(3, np.float64)
+    r = LrrResult()
+    r.Z = ctypes.c_void_p(Z.data_ptr()) if Z is not None else None
+    r.S = ctypes.c_void_p(S.data_ptr()) if S is not None else None
+    r.iters = iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    r.resid = resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    r.ranks = ranks.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    r.timings_ms = tim.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    stream = torch.cuda.current_stream(M.device).cuda_stream
+    code = getattr(lib, entry)(ctypes.byref(p), ctypes.byref(opts), ctypes.c_void_p(workspace.data_ptr()),
+                               ctypes.c_size_t(workspace.numel()), ctypes.byref(r), ctypes.c_void_p(stream))
+    if code < 0 and raise_on_error:
+        raise LrrError(code)
+    return SolveResult(Z=Z, S=S, iters=iters, resid=resid, rank_M=int(ranks[0]), k1=int(ranks[1]),
+                       block_ranks=ranks[2:].copy(), timings_ms=tim, status=int(code))
+
+
+def dfc_lrr_solve(M, perm, offsets, opts: LrrOptions, **kw) -> SolveResult:
+    """Algorithm 1 through the C ABI (see include/dfc_lrr.h)."""
+    return _solve("dfc_lrr_solve", M, perm, offsets, opts, **kw)
+
+
+def lrr_solve(M, perm, opts: LrrOptions, **kw) -> SolveResult:
+    """Eq. (1) through the C ABI: one block holding every column in `perm` order."""
+    n = M.shape[1]
+    return _solve("lrr_solve", M, perm, np.array([0, n], np.int64), opts, **kw)

@@ -1,0 +1,373 @@
+// Element-wise and per-block kernels of the inexact ALM iteration (reduced
+// coordinates).  Included by solver.cu only.
+//
+// Reduced coordinates: with M = U diag(sigma) V^T (compact, rank r) every ALM
+// iterate starting from zero keeps its columns in range(M^T) = range(V)
+// (the SVT, (I + M^T M)^{-1} and the dual steps all map range(V) into
+// itself), so Z = V Zt, J = V Jt, Y2 = V Y2t with r x l blocks Zt, Jt, Y2t:
+//   SVT:      Jt = SVT_{1/mu}(Zt + Y2t/mu)         (SVT commutes with V)
+//   Z-step:   Zt = (sigma (U^T P) + Jt - Y2t/mu) / (1 + sigma^2),  P = C - E + Y1/mu
+//   M Z   =   U diag(sigma) Zt
+// E, Y1 and the residual C - M Z - E stay in the m-dimensional data space.
+#pragma once
+#include "common.cuh"
+
+namespace lrr {
+namespace k {
+
+template <typename T, typename Tin>
+__global__ void gather_cols(const Tin* __restrict__ M, int64_t ldm, const int64_t* __restrict__ perm, int64_t m,
+                            int64_t n, T* __restrict__ C) {
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
+        const Tin* src = M + (perm ? perm[j] : j) * ldm;
+        T* dst = C + j * m;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+            dst[i] = (T)src[i];
+    }
+}
+
+template <typename Tin>
+__global__ void nonfinite_check(const Tin* __restrict__ M, int64_t ldm, int64_t m, int64_t n, int* flag) {
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y)
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+            const Tin v = M[i + j * ldm];
+            if (!isfinite(v)) *flag = 1;
+        }
+}
+
+template <typename T>
+__global__ void fill(T* __restrict__ x, int64_t count, T v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+template <typename T>
+__global__ void copy_convert_f64(const double* __restrict__ src, T* __restrict__ dst, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (T)src[i];
+}
+
+template <typename T>
+__global__ void copy_convert_to_f64(const T* __restrict__ src, double* __restrict__ dst, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i];
+}
+
+// square pp x pp matrix, ld pp: real part p x p is left alone; padding gets
+// `diag` on the diagonal and zeros elsewhere.  With eye != 0 the real part is
+// set to the identity too (eigenvector matrices).
+template <typename T>
+__global__ void init_padded(T* __restrict__ G, int p, int pp, T diag, int eye) {
+    const int64_t count = (int64_t)pp * pp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % pp), j = (int)(e / pp);
+        if (i < p && j < p) {
+            if (eye) G[e] = (i == j) ? T(1) : T(0);
+        } else {
+            G[e] = (i == j) ? diag : T(0);
+        }
+    }
+}
+
+// Per-block SVT gate: trace(G) <= tau^2 means every eigenvalue of the Gram is
+// <= tau^2, so the threshold removes all singular values and J = 0 without
+// an eigendecomposition.  Also records max |G_ii| (the Jacobi noise floor).
+template <typename T>
+__global__ void svt_gate(T* const* __restrict__ G, const int* __restrict__ p, const int* __restrict__ pp,
+                         const int* __restrict__ act, const double* __restrict__ mu, int* __restrict__ svt_on,
+                         T* __restrict__ scale, int nblk) {
+    const int b = blockIdx.x;
+    if (b >= nblk) return;
+    if (!act[b]) {
+        if (threadIdx.x == 0) svt_on[b] = 0;
+        return;
+    }
+    const T* g = G[b];
+    const int n = p[b], ld = pp[b];
+    double tr = 0.0;
+    T mx = T(0);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const T v = g[i + (int64_t)i * ld];
+        tr += (double)v;
+        mx = fmax(mx, fabs(v));
+    }
+    __shared__ double s_tr[32];
+    __shared__ T s_mx[32];
+    tr = warp_sum(tr);
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0) { s_tr[threadIdx.x >> 5] = tr; s_mx[threadIdx.x >> 5] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        T m2 = T(0);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += s_tr[w]; m2 = fmax(m2, s_mx[w]); }
+        const double tau = 1.0 / mu[b];
+        svt_on[b] = a > tau * tau ? 1 : 0;
+        scale[b] = m2;
+    }
+}
+
+// h_j = max(1 - tau/sqrt(lambda_j), 0) from the Gram eigenvalues lambda_j =
+// diag(G) after Jacobi; J = A W diag(h) W^T (tall) or W diag(h) W^T A (wide)
+// equals U max(Sigma - tau, 0) V^T.  Also counts the SVT rank.
+template <typename T>
+__global__ void svt_weights(T* const* __restrict__ G, T* const* __restrict__ h, const int* __restrict__ p,
+                            const int* __restrict__ pp, const int* __restrict__ act, const int* __restrict__ svt_on,
+                            const double* __restrict__ mu, int* __restrict__ rank, int nblk) {
+    const int b = blockIdx.x;
+    if (b >= nblk || !act[b]) return;
+    const T* g = G[b];
+    T* hb = h[b];
+    const int n = p[b], ld = pp[b];
+    const double tau = 1.0 / mu[b];
+    const T tau_t = (T)tau;
+    const T tau2 = (T)(tau * tau);
+    const int on = svt_on[b];
+    int cnt = 0;
+    for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+        T w = T(0);
+        if (on && i < n) {
+            const T lam = g[i + (int64_t)i * ld];
+            if (lam > tau2) {
+                w = T(1) - tau_t / sqrt(lam);
+                if (w > T(0)) ++cnt; else w = T(0);
+            }
+        }
+        hb[i] = w;
+    }
+    __shared__ int s_c[32];
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if ((threadIdx.x & 31) == 0) s_c[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int a = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += s_c[w];
+        rank[b] = a;
+    }
+}
+
+// Z-step in reduced coordinates, fused with the Y2 dual step and the next
+// SVT input; one warp per column.
+template <typename T>
+__global__ void z_update(int r, int64_t n, const int* __restrict__ colblk, const int* __restrict__ act,
+                         const double* __restrict__ mu, double rho, double mu_max, const T* __restrict__ Tt,
+                         const T* __restrict__ Jt, T* __restrict__ Y2t, T* __restrict__ Zt, T* __restrict__ D,
+                         T* __restrict__ A, const T* __restrict__ sig, const T* __restrict__ dinv,
+                         T* __restrict__ dmax) {
+    const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= n) return;
+    const int b = colblk[j];
+    if (!act[b]) return;
+    const double mud = mu[b];
+    const double mun = fmin(rho * mud, mu_max);
+    const T imu = (T)(1.0 / mud), muT = (T)mud, imun = (T)(1.0 / mun);
+    const int64_t o = j * r;
+    T acc = T(0);
+    for (int i = lane; i < r; i += 32) {
+        const T tv = Tt[o + i], jv = Jt[o + i], y2 = Y2t[o + i];
+        const T z = dinv[i] * (sig[i] * tv + jv - y2 * imu);
+        const T dd = z - jv;
+        const T y2n = y2 + muT * dd;
+        Zt[o + i] = z;
+        D[o + i] = dd;
+        Y2t[o + i] = y2n;
+        A[o + i] = z + y2n * imun;
+        acc += dd * dd;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) atomic_max_nonneg(&dmax[b], sqrt(acc));
+}
+
+// E-step (column shrinkage), primal residual, Y1 dual step and the next
+// Z-step right-hand side P = C - E + Y1/mu'; one warp per column.
+template <typename T>
+__global__ void e_update(int64_t m, int64_t n, const int* __restrict__ colblk, const int* __restrict__ act,
+                         const double* __restrict__ mu, double rho, double mu_max, double lam,
+                         const T* __restrict__ C, const T* __restrict__ MZ, T* __restrict__ Y1, T* __restrict__ E,
+                         T* __restrict__ P, T* __restrict__ r1max) {
+    const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= n) return;
+    const int b = colblk[j];
+    if (!act[b]) return;
+    const double mud = mu[b];
+    const double mun = fmin(rho * mud, mu_max);
+    const T imu = (T)(1.0 / mud), muT = (T)mud, imun = (T)(1.0 / mun);
+    const T thr = (T)(lam / mud);
+    const int64_t o = j * m;
+    T acc = T(0);
+    for (int64_t i = lane; i < m; i += 32) {
+        const T x = C[o + i] - MZ[o + i] + Y1[o + i] * imu;
+        acc += x * x;
+    }
+    const T nrm = sqrt(warp_sum(acc));
+    const T sc = nrm > thr ? T(1) - thr / nrm : T(0);
+    T amax = T(0);
+    for (int64_t i = lane; i < m; i += 32) {
+        const T c = C[o + i], mz = MZ[o + i], y1 = Y1[o + i];
+        const T x = c - mz + y1 * imu;
+        const T e = sc * x;
+        const T l1 = c - mz - e;
+        const T y1n = y1 + muT * l1;
+        E[o + i] = e;
+        Y1[o + i] = y1n;
+        P[o + i] = c - e + y1n * imun;
+        amax = fmax(amax, fabs(l1));
+    }
+    amax = warp_max(amax);
+    if (lane == 0) atomic_max_nonneg(&r1max[b], amax);
+}
+
+// Stop test, part 1: ||C - M Z - E||_inf < eps is necessary.  ||Z - J||_inf =
+// max |V D| <= nu * max_j ||D_j|| (nu = largest row norm of V) decides
+// convergence when that bound is already below eps; otherwise the exact value
+// is needed (a product with V).
+template <typename T>
+__global__ void stop_part1(int nblk, const int* __restrict__ act, const T* __restrict__ r1, const T* __restrict__ dmax,
+                           T nu, double eps, int* __restrict__ need_exact, int* __restrict__ conv_bound) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblk) return;
+    int ne = 0, cb = 0;
+    if (act[b] && (double)r1[b] < eps) {
+        if ((double)(nu * dmax[b]) < eps) cb = 1; else ne = 1;
+    }
+    need_exact[b] = ne;
+    conv_bound[b] = cb;
+}
+
+template <typename T>
+__global__ void stop_part2(int nblk, int* __restrict__ act, int* __restrict__ iters, double* __restrict__ mu,
+                           double rho, double mu_max, double eps, int max_iter, T* __restrict__ r1,
+                           T* __restrict__ dmax, T* __restrict__ r2x, const int* __restrict__ need_exact,
+                           const int* __restrict__ conv_bound, T nu, double* __restrict__ resid,
+                           const int* __restrict__ rank_cur, int* __restrict__ rank_fin, int* __restrict__ conv,
+                           double* __restrict__ mu_fin) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblk) return;
+    if (act[b]) {
+        const int it = ++iters[b];
+        const bool ok = conv_bound[b] || (need_exact[b] && (double)r2x[b] < eps);
+        const double rz = need_exact[b] ? (double)r2x[b] : (double)(nu * dmax[b]);
+        resid[2 * b] = (double)r1[b];
+        resid[2 * b + 1] = rz;
+        rank_fin[b] = rank_cur[b];
+        mu_fin[b] = mu[b];
+        if (ok || it >= max_iter) {
+            act[b] = 0;
+            conv[b] = ok ? 1 : 0;
+        } else {
+            mu[b] = fmin(rho * mu[b], mu_max);
+        }
+    }
+    r1[b] = T(0);
+    dmax[b] = T(0);
+    r2x[b] = T(0);
+}
+
+// one-time factor M M^T = W diag(lam) W^T (columns of W in `order`, the r
+// kept ones): U (float64), U diag(1/sigma) (for V = M^T U diag(1/sigma))
+__global__ void setup_factors(const double* __restrict__ W, int64_t ldw, int64_t m, int r,
+                              const int* __restrict__ order, const double* __restrict__ lam, double* __restrict__ Ud,
+                              double* __restrict__ Usd) {
+    const int k = blockIdx.y;
+    if (k >= r) return;
+    const int src = order[k];
+    const double s = sqrt(fmax(lam[k], 0.0));
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const double u = W[i + (int64_t)src * ldw];
+        Ud[i + k * m] = u;
+        Usd[i + k * m] = u / s;
+    }
+}
+
+template <typename T>
+__global__ void diag_of(const T* __restrict__ G, int64_t ld, int64_t count, double* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count) out[i] = (double)G[i + i * ld];
+}
+
+// sigma, 1/(1+sigma^2), U and U diag(sigma) in the iteration's precision
+template <typename T>
+__global__ void setup_scalars(const double* __restrict__ lam, int r, const double* __restrict__ Ud, int64_t m,
+                              T* __restrict__ sig, T* __restrict__ dinv, T* __restrict__ U, T* __restrict__ US) {
+    const int k = blockIdx.y;
+    if (k >= r) return;
+    const double s = sqrt(fmax(lam[k], 0.0));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sig[k] = (T)s;
+        dinv[k] = (T)(1.0 / (1.0 + s * s));
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const double u = Ud[i + k * m];
+        U[i + k * m] = (T)u;
+        US[i + k * m] = (T)(u * s);
+    }
+}
+
+// largest row 2-norm of V (n x r): nu in the bound |v_i . d| <= ||v_i|| ||d||
+template <typename T>
+__global__ void row_norm_max(const T* __restrict__ V, int64_t n, int r, T* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = 0.0;
+    for (int k = 0; k < r; ++k) {
+        const double v = (double)V[i + k * n];
+        acc += v * v;
+    }
+    atomic_max_nonneg(out, (T)(sqrt(acc) * (1.0 + 1e-6)));
+}
+
+template <typename T>
+__global__ void scatter_cols(const T* __restrict__ src, int64_t m, int64_t n, const int64_t* __restrict__ perm,
+                             T* __restrict__ dst) {
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y)
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+            dst[i + perm[j] * m] = src[i + j * m];
+}
+
+// C-step helpers -----------------------------------------------------------
+// keep-list of the kept SVT directions (h > 0) of block 0
+template <typename T>
+__global__ void kept_columns(const T* __restrict__ h, int p, int* __restrict__ idx, int* __restrict__ count) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int c = 0;
+    for (int i = 0; i < p; ++i)
+        if (h[i] > T(0)) idx[c++] = i;
+    *count = c;
+}
+
+// F64 copy of selected columns of a (rows x ?) matrix, normalised to unit norm
+template <typename T>
+__global__ void gather_normalise_f64(const T* __restrict__ src, int64_t ld, int64_t rows, const int* __restrict__ idx,
+                                     const int* __restrict__ count, double* __restrict__ dst) {
+    const int k = blockIdx.x;
+    if (k >= *count) return;
+    const T* s = src + (int64_t)idx[k] * ld;
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) {
+        const double v = (double)s[i];
+        acc += v * v;
+    }
+    __shared__ double red[32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) red[0] = v;
+    }
+    __syncthreads();
+    const double inv = red[0] > 0.0 ? 1.0 / sqrt(red[0]) : 0.0;
+    for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) dst[i + (int64_t)k * rows] = (double)s[i] * inv;
+}
+
+// X <- 1.5 X - 0.5 Y  (Newton-Schulz step for the polar factor, Y = X X^T X)
+__global__ void ns_combine(double* __restrict__ X, const double* __restrict__ Y, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        X[i] = 1.5 * X[i] - 0.5 * Y[i];
+}
+
+}  // namespace k
+}  // namespace lrr

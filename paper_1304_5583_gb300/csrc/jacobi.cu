@@ -1,0 +1,255 @@
+// Batched block-Jacobi eigensolver for symmetric matrices (float32 / float64).
+//
+// The SVT of every ALM iteration needs the eigendecomposition of a Gram
+// matrix, and the one-time factor needs that of M M^T.  Cyclic block Jacobi
+// keeps the work in dense 2b x 2b tiles: in every round the diagonal blocks
+// are paired round-robin, each CTA diagonalises one 2b x 2b pivot submatrix
+// in shared memory (inner cyclic Jacobi with the classical rotation angle),
+// and a second kernel applies the accumulated rotations R_P to the
+// off-diagonal tiles (G <- R^T G R) and to the eigenvector matrix (W <- W R).
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace lrr {
+namespace {
+
+constexpr int NT = 256;
+
+// item at position `pos` of round `r` in the circle-method schedule of N items
+__device__ __forceinline__ int circle_item(int pos, int r, int N) {
+    return pos == 0 ? 0 : 1 + ((pos - 1 + r) % (N - 1));
+}
+
+// global row of local index i (0..2b-1) of the pivot pair (a, c)
+__device__ __forceinline__ int pair_row(int i, int a, int c, int b) { return i < b ? a * b + i : c * b + (i - b); }
+
+template <typename T, int B2>
+__global__ void __launch_bounds__(NT) jac_solve(const JacDesc<T>* __restrict__ descs, int round, T tol) {
+    constexpr int b = B2 / 2;
+    const JacDesc<T> d = descs[blockIdx.y];
+    if (d.active && *d.active == 0) return;
+    if (*d.done) return;
+    const int nb = d.pp / b, npairs = nb / 2;
+    const int P = blockIdx.x;
+    if (P >= npairs) return;
+    const int a = circle_item(P, round, nb), c = circle_item(nb - 1 - P, round, nb);
+
+    __shared__ T S[B2][B2 + 1];
+    __shared__ T R[B2][B2 + 1];
+    __shared__ T cs[b], sn[b];
+    __shared__ int pi[b], qi[b];
+    __shared__ T red[NT / 32];
+    const int t = threadIdx.x;
+    const T floor_abs = num<T>::eps() * (*d.scale) + num<T>::tiny();
+
+    for (int e = t; e < B2 * B2; e += NT) {
+        const int i = e % B2, j = e / B2;
+        S[i][j] = d.G[pair_row(i, a, c, b) + (int64_t)pair_row(j, a, c, b) * d.pp];
+        R[i][j] = (i == j) ? T(1) : T(0);
+    }
+    __syncthreads();
+
+    // convergence measure of this pivot block before rotating it
+    T offm = T(0);
+    for (int e = t; e < B2 * B2; e += NT) {
+        const int i = e % B2, j = e / B2;
+        if (i < j) {
+            const T v = fabs(S[i][j]);
+            if (v > floor_abs) offm = fmax(offm, v / sqrt(fabs(S[i][i] * S[j][j]) + num<T>::tiny()));
+        }
+    }
+    offm = warp_max(offm);
+    if ((t & 31) == 0) red[t >> 5] = offm;
+    __syncthreads();
+    if (t == 0) {
+        T mx = T(0);
+        for (int w = 0; w < NT / 32; ++w) mx = fmax(mx, red[w]);
+        atomic_max_nonneg(d.off, mx);
+        red[0] = mx;
+    }
+    __syncthreads();
+    const bool need = red[0] > tol;
+
+    if (need) {
+        for (int sweep = 0; sweep < 6; ++sweep) {
+            int rotated = 0;
+            for (int r = 0; r < B2 - 1; ++r) {
+                if (t < b) {
+                    const int p = circle_item(t, r, B2), q = circle_item(B2 - 1 - t, r, B2);
+                    const T app = S[p][p], aqq = S[q][q], apq = S[p][q];
+                    T cc = T(1), ss = T(0);
+                    if (fabs(apq) > floor_abs && fabs(apq) > num<T>::eps() * sqrt(fabs(app * aqq))) {
+                        const T theta = (aqq - app) / (T(2) * apq);
+                        T tt;
+                        if (fabs(theta) > T(1) / num<T>::eps()) tt = T(0.5) / theta;
+                        else tt = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+                        cc = T(1) / sqrt(tt * tt + T(1));
+                        ss = tt * cc;
+                        rotated = 1;
+                    }
+                    cs[t] = cc; sn[t] = ss; pi[t] = p; qi[t] = q;
+                }
+                __syncthreads();
+                // S <- J^T S J on all 2x2 sub-blocks at once; R <- R J
+                for (int e = t; e < b * b; e += NT) {
+                    const int k = e % b, l = e / b;
+                    const int p = pi[k], q = qi[k], u = pi[l], v = qi[l];
+                    const T ck = cs[k], sk = sn[k], cl = cs[l], sl = sn[l];
+                    const T s_pu = S[p][u], s_pv = S[p][v], s_qu = S[q][u], s_qv = S[q][v];
+                    // rows: (J^T S)
+                    const T r_pu = ck * s_pu - sk * s_qu, r_pv = ck * s_pv - sk * s_qv;
+                    const T r_qu = sk * s_pu + ck * s_qu, r_qv = sk * s_pv + ck * s_qv;
+                    // columns: (.. J)
+                    S[p][u] = cl * r_pu - sl * r_pv;
+                    S[p][v] = sl * r_pu + cl * r_pv;
+                    S[q][u] = cl * r_qu - sl * r_qv;
+                    S[q][v] = sl * r_qu + cl * r_qv;
+                }
+                for (int e = t; e < B2 * b; e += NT) {
+                    const int i = e % B2, l = e / B2;
+                    const int u = pi[l], v = qi[l];
+                    const T cl = cs[l], sl = sn[l];
+                    const T x = R[i][u], y = R[i][v];
+                    R[i][u] = cl * x - sl * y;
+                    R[i][v] = sl * x + cl * y;
+                }
+                __syncthreads();
+                if (t < b && sn[t] != T(0)) { S[pi[t]][qi[t]] = T(0); S[qi[t]][pi[t]] = T(0); }
+                __syncthreads();
+            }
+            if (!__syncthreads_or(rotated)) break;
+        }
+    }
+    // diagonalised pivot block back into G, rotation out for the apply kernel
+    T* Rg = d.R + (int64_t)P * B2 * B2;
+    for (int e = t; e < B2 * B2; e += NT) {
+        const int i = e % B2, j = e / B2;
+        if (need) d.G[pair_row(i, a, c, b) + (int64_t)pair_row(j, a, c, b) * d.pp] = S[i][j];
+        Rg[e] = R[i][j];
+    }
+}
+
+template <typename T, int B2>
+__global__ void __launch_bounds__(NT) jac_apply(const JacDesc<T>* __restrict__ descs, int round) {
+    constexpr int b = B2 / 2;
+    const JacDesc<T> d = descs[blockIdx.y];
+    if (d.active && *d.active == 0) return;
+    if (*d.done) return;
+    const int nb = d.pp / b, npairs = nb / 2;
+    const int ntile_g = npairs * (npairs - 1) / 2;
+    int tile = blockIdx.x;
+    if (tile >= ntile_g + npairs * npairs) return;
+
+    __shared__ T X[B2][B2 + 1];
+    __shared__ T Q[B2][B2 + 1];
+    const int t = threadIdx.x;
+    // each thread owns 16 (B2=64) or 4 (B2=32) output entries: rows i0 + 16*ii, cols tj
+    constexpr int PER = B2 * B2 / NT;
+
+    if (tile < ntile_g) {
+        // off-diagonal tile (P, Q), P < Q:  G[I_P, I_Q] <- R_P^T G[I_P, I_Q] R_Q
+        int P = 0, rem = tile;
+        while (rem >= npairs - 1 - P) { rem -= npairs - 1 - P; ++P; }
+        const int Qp = P + 1 + rem;
+        const int a = circle_item(P, round, nb), c = circle_item(nb - 1 - P, round, nb);
+        const int a2 = circle_item(Qp, round, nb), c2 = circle_item(nb - 1 - Qp, round, nb);
+        const T* RP = d.R + (int64_t)P * B2 * B2;
+        const T* RQ = d.R + (int64_t)Qp * B2 * B2;
+        for (int e = t; e < B2 * B2; e += NT) {
+            const int i = e % B2, j = e / B2;
+            X[i][j] = d.G[pair_row(i, a, c, b) + (int64_t)pair_row(j, a2, c2, b) * d.pp];
+            Q[i][j] = RQ[e];
+        }
+        __syncthreads();
+        T acc[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e = t + u * NT, i = e % B2, j = e / B2;
+            T s = T(0);
+#pragma unroll 8
+            for (int k = 0; k < B2; ++k) s = fma(X[i][k], Q[k][j], s);
+            acc[u] = s;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e = t + u * NT, i = e % B2, j = e / B2;
+            X[i][j] = acc[u];
+            Q[i][j] = RP[e];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e = t + u * NT, i = e % B2, j = e / B2;
+            T s = T(0);
+#pragma unroll 8
+            for (int k = 0; k < B2; ++k) s = fma(Q[k][i], X[k][j], s);
+            const int gi = pair_row(i, a, c, b), gj = pair_row(j, a2, c2, b);
+            d.G[gi + (int64_t)gj * d.pp] = s;
+            d.G[gj + (int64_t)gi * d.pp] = s;
+        }
+    } else {
+        // eigenvector tile: rows chunk ch, columns I_P:  W[ch, I_P] <- W[ch, I_P] R_P
+        tile -= ntile_g;
+        const int P = tile % npairs, ch = tile / npairs;
+        const int a = circle_item(P, round, nb), c = circle_item(nb - 1 - P, round, nb);
+        const T* RP = d.R + (int64_t)P * B2 * B2;
+        for (int e = t; e < B2 * B2; e += NT) {
+            const int i = e % B2, j = e / B2;
+            X[i][j] = d.W[(ch * B2 + i) + (int64_t)pair_row(j, a, c, b) * d.pp];
+            Q[i][j] = RP[e];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e = t + u * NT, i = e % B2, j = e / B2;
+            T s = T(0);
+#pragma unroll 8
+            for (int k = 0; k < B2; ++k) s = fma(X[i][k], Q[k][j], s);
+            d.W[(ch * B2 + i) + (int64_t)pair_row(j, a, c, b) * d.pp] = s;
+        }
+    }
+}
+
+template <typename T>
+__global__ void jac_reset(const JacDesc<T>* __restrict__ descs, int nmat) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nmat) return;
+    *descs[i].done = 0;
+    *descs[i].off = T(0);
+}
+
+template <typename T>
+__global__ void jac_check(const JacDesc<T>* __restrict__ descs, int nmat, T tol) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nmat) return;
+    const JacDesc<T> d = descs[i];
+    if (*d.done == 0 && *d.off <= tol) *d.done = 1;
+    *d.off = T(0);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t jacobi_sweeps(const JacDesc<T>* d_desc, int nmat, int max_pp, int sweeps, T tol, cudaStream_t s) {
+    constexpr int b = jacobi_bs<T>();
+    constexpr int B2 = 2 * b;
+    if (nmat <= 0 || max_pp <= 0) return cudaSuccess;
+    const int nb = max_pp / b, npairs = nb / 2;
+    jac_reset<T><<<ceil_div(nmat, 128), 128, 0, s>>>(d_desc, nmat);
+    const dim3 gs((unsigned)npairs, (unsigned)nmat);
+    const dim3 ga((unsigned)(npairs * (npairs - 1) / 2 + npairs * npairs), (unsigned)nmat);
+    for (int sw = 0; sw < sweeps; ++sw) {
+        for (int r = 0; r < nb - 1; ++r) {
+            jac_solve<T, B2><<<gs, NT, 0, s>>>(d_desc, r, tol);
+            if (npairs > 1 || true) jac_apply<T, B2><<<ga, NT, 0, s>>>(d_desc, r);
+        }
+        jac_check<T><<<ceil_div(nmat, 128), 128, 0, s>>>(d_desc, nmat, tol);
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t jacobi_sweeps<float>(const JacDesc<float>*, int, int, int, float, cudaStream_t);
+template cudaError_t jacobi_sweeps<double>(const JacDesc<double>*, int, int, int, double, cudaStream_t);
+
+}  // namespace lrr

@@ -1,0 +1,55 @@
+// Launchers of the DFC-LRR kernels (one translation unit per family).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lrr {
+
+// ---------------------------------------------------------------- grouped GEMM
+// C_g = alpha * op(A_g) * op(B_g) + beta * C_g for every group g whose flag is
+// nonzero (flag == nullptr: always).  Column-major, op = transpose if trans*.
+// ccol (optional, device, int64): column j of the product is stored at column
+// ccol[j] of C (used to undo the D-step permutation).
+template <typename T>
+struct GemmDesc {
+    const T* A;
+    const T* B;
+    T* C;
+    const int* flag;
+    const int64_t* ccol;
+    const T* kscale;      // optional: op(A)(i,k) is multiplied by kscale[k]
+    T* absmax;            // optional: store nothing, atomically max |alpha op(A) op(B)| here
+    int64_t lda, ldb, ldc;
+    int m, n, k;
+    T alpha, beta;
+};
+
+template <typename T>
+cudaError_t gemm_grouped(const GemmDesc<T>* d_desc, int groups, bool transA, bool transB, int max_m, int max_n,
+                         cudaStream_t s);
+
+// ---------------------------------------------------------- batched Jacobi eig
+// Symmetric matrices G_i (pp_i x pp_i, ld pp_i, pp_i a multiple of 2*bs) are
+// reduced to diagonal form in place by block Jacobi rotations, accumulated into
+// W_i (pp_i x pp_i, ld pp_i): on exit G_in = W diag(G_out) W^T.
+template <typename T>
+struct JacDesc {
+    T* G;
+    T* W;
+    T* R;          // rotation scratch: (pp/(2bs)) * (2bs)^2 values
+    int* done;     // per matrix: 1 when converged (checked before each sweep)
+    T* off;        // per matrix: max scaled off-diagonal seen in the current sweep
+    const int* active;  // optional: skip when *active == 0
+    const T* scale;     // per matrix: max |G_ii| at entry (off-diagonals below eps*scale are zero)
+    int pp;        // padded order (multiple of 2*bs)
+};
+
+// Runs up to `sweeps` cyclic block-Jacobi sweeps (round-robin pairing of the
+// pp/bs diagonal blocks) on every matrix; a matrix stops once a whole sweep
+// saw no scaled off-diagonal |G_ij|/sqrt(G_ii G_jj) above tol.  bs = 16 for
+// double, 32 for float.  `done` and `off` are reset at entry.
+template <typename T>
+cudaError_t jacobi_sweeps(const JacDesc<T>* d_desc, int nmat, int max_pp, int sweeps, T tol, cudaStream_t s);
+template <typename T> constexpr int jacobi_bs() { return sizeof(T) == 8 ? 16 : 32; }
+
+}  // namespace lrr

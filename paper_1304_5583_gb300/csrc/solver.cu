@@ -1,0 +1,665 @@
+// DFC-LRR solver: host orchestration and the C ABI declared in dfc_lrr.h.
+//
+// Flow of one call (Algorithm 1, Section 2.2):
+//   checks            -> non-finite scan of M, partition validation
+//   one-time factor   -> K = M M^T (float64), block-Jacobi eigendecomposition
+//                        K = U diag(sigma^2) U^T, rank r, V = M^T U diag(1/sigma).
+//                        This factors I + M^T M = V diag(1+sigma^2) V^T + (I - V V^T)
+//                        once for every block, because all blocks share the
+//                        dictionary M (eq. (2)).
+//   F step            -> the t block problems advance together: every launch
+//                        covers all still-active blocks (per-block penalty mu_i,
+//                        stop flag and iteration count); `batched = 0` runs the
+//                        same kernels on one block at a time.
+//   C step            -> column projection onto the column space of Z_1
+//                        (orthonormal basis of J_1's factored form), then the
+//                        D-step permutation is undone while writing Z and S.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <numeric>
+#include <type_traits>
+#include <vector>
+
+#include "dfc_lrr.h"
+#include "alm_kernels.cuh"
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace lrr {
+namespace {
+
+constexpr size_t kAlign = 256;
+
+struct Arena {
+    char* base;
+    size_t off = 0;
+    explicit Arena(void* b) : base(static_cast<char*>(b)) {}
+    template <typename X>
+    X* take(size_t count) {
+        off = (off + kAlign - 1) / kAlign * kAlign;
+        X* p = base ? reinterpret_cast<X*>(base + off) : nullptr;
+        off += std::max<size_t>(count, 1) * sizeof(X);
+        return p;
+    }
+};
+
+inline int round_up(int x, int q) { return (x + q - 1) / q * q; }
+
+bool valid_problem(const lrr_problem* p, const lrr_options* o) {
+    if (!p || !o || !p->M || !p->perm || !p->offsets) return false;
+    if (p->m < 1 || p->n < 1 || p->ldm < p->m || p->t < 1 || p->t > p->n) return false;
+    if (p->m > (1 << 20) || p->n > (1 << 24)) return false;
+    if (p->offsets[0] != 0 || p->offsets[p->t] != p->n) return false;
+    for (int i = 0; i < p->t; ++i)
+        if (p->offsets[i + 1] <= p->offsets[i]) return false;
+    std::vector<char> seen((size_t)p->n, 0);
+    for (int64_t j = 0; j < p->n; ++j) {
+        const int64_t c = p->perm[j];
+        if (c < 0 || c >= p->n || seen[(size_t)c]) return false;
+        seen[(size_t)c] = 1;
+    }
+    if (!(o->lambda > 0) || !(o->rho > 1) || !(o->mu0 > 0) || !(o->mu_max >= o->mu0) || !(o->eps > 0)) return false;
+    if (o->max_iter < 1) return false;
+    if (o->precision < LRR_PREC_F64 || o->precision > LRR_PREC_MIXED) return false;
+    return true;
+}
+
+template <typename T>
+struct BlockInfo {
+    int64_t col0;
+    int l, pmax, ppmax;
+};
+
+// Every device array of one solve, carved from the workspace.
+template <typename T>
+struct Buffers {
+    int64_t m, n;
+    int t, rmax, mpp;
+    // one-time factor (float64)
+    double *Md, *Kd, *Wd, *Rd, *Dd, *lam_raw, *lam, *Ud, *Usd, *Vd;
+    double *jac_off_d, *jac_scale_d;
+    int *jac_done_d, *order;
+    JacDesc<double>* jac_setup;
+    // factor in the iteration precision
+    T *U, *US, *sig, *dinv, *V, *nu;
+    // state (m x n) and reduced state (rmax x n)
+    T *C, *P, *MZ, *E, *Y1;
+    T *Zt, *Jt, *Y2t, *A, *D, *Tt;
+    // per block
+    std::vector<T*> G, W, H, R, h, T1;
+    double *mu, *mu_fin, *resid;
+    int *act, *iters, *svt_on, *rank_cur, *rank_fin, *need_exact, *conv_bound, *conv, *jdone, *colblk, *flag;
+    T *r1, *dmax, *r2x, *jscale, *joff;
+    int64_t* perm;
+    // descriptor / pointer tables
+    GemmDesc<T>* gd;       // 12 * t descriptors
+    JacDesc<T>* jd;
+    T** Gp;
+    T** hp;
+    int *pv, *ppv;
+    // C step
+    int *kept, *kept_n;
+    double *Fd, *Gk, *Yd;
+    T *Q, *Wc;
+};
+
+template <typename T>
+Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector<BlockInfo<T>>& blk) {
+    Buffers<T> b{};
+    b.m = p->m;
+    b.n = p->n;
+    b.t = p->t;
+    b.rmax = (int)std::min<int64_t>(p->m, p->n);
+    constexpr int B2d = 2 * jacobi_bs<double>();
+    constexpr int B2 = 2 * jacobi_bs<T>();
+    b.mpp = round_up((int)p->m, B2d);
+    const int64_t m = p->m, n = p->n, r = b.rmax, mpp = b.mpp;
+    b.Md = need_md ? a.take<double>(m * n) : nullptr;
+    b.Kd = a.take<double>(mpp * mpp);
+    b.Wd = a.take<double>(mpp * mpp);
+    b.Rd = a.take<double>(mpp * B2d);
+    b.lam_raw = a.take<double>(m);
+    b.lam = a.take<double>(m);
+    b.order = a.take<int>(m);
+    b.Ud = a.take<double>(m * r);
+    b.Usd = a.take<double>(m * r);
+    b.Vd = a.take<double>(n * r);
+    b.jac_off_d = a.take<double>(1);
+    b.jac_scale_d = a.take<double>(1);
+    b.jac_done_d = a.take<int>(1);
+    b.jac_setup = a.take<JacDesc<double>>(1);
+    b.U = a.take<T>(m * r);
+    b.US = a.take<T>(m * r);
+    b.sig = a.take<T>(r);
+    b.dinv = a.take<T>(r);
+    b.V = a.take<T>(n * r);
+    b.nu = a.take<T>(1);
+    b.C = a.take<T>(m * n);
+    b.P = a.take<T>(m * n);
+    b.MZ = a.take<T>(m * n);
+    b.E = a.take<T>(m * n);
+    b.Y1 = a.take<T>(m * n);
+    b.Zt = a.take<T>(r * n);
+    b.Jt = a.take<T>(r * n);
+    b.Y2t = a.take<T>(r * n);
+    b.A = a.take<T>(r * n);
+    b.D = a.take<T>(r * n);
+    b.Tt = a.take<T>(r * n);
+    const int t = p->t;
+    b.G.resize(t); b.W.resize(t); b.H.resize(t); b.R.resize(t); b.h.resize(t); b.T1.resize(t);
+    for (int i = 0; i < t; ++i) {
+        const int64_t pp = blk[i].ppmax;
+        b.G[i] = a.take<T>(pp * pp);
+        b.W[i] = a.take<T>(pp * pp);
+        b.H[i] = a.take<T>(pp * pp);
+        b.T1[i] = a.take<T>(pp * pp);
+        b.R[i] = a.take<T>(pp * B2);
+        b.h[i] = a.take<T>(pp);
+    }
+    b.mu = a.take<double>(t);
+    b.mu_fin = a.take<double>(t);
+    b.resid = a.take<double>(2 * t);
+    b.act = a.take<int>(t);
+    b.iters = a.take<int>(t);
+    b.svt_on = a.take<int>(t);
+    b.rank_cur = a.take<int>(t);
+    b.rank_fin = a.take<int>(t);
+    b.need_exact = a.take<int>(t);
+    b.conv_bound = a.take<int>(t);
+    b.conv = a.take<int>(t);
+    b.jdone = a.take<int>(t);
+    b.colblk = a.take<int>(n);
+    b.flag = a.take<int>(4);
+    b.r1 = a.take<T>(t);
+    b.dmax = a.take<T>(t);
+    b.r2x = a.take<T>(t);
+    b.jscale = a.take<T>(t);
+    b.joff = a.take<T>(t);
+    b.perm = a.take<int64_t>(n);
+    b.gd = a.take<GemmDesc<T>>(16 * (size_t)t + 16);
+    b.jd = a.take<JacDesc<T>>(t);
+    b.Gp = a.take<T*>(t);
+    b.hp = a.take<T*>(t);
+    b.pv = a.take<int>(t);
+    b.ppv = a.take<int>(t);
+    const int64_t p0 = blk[0].ppmax;
+    b.kept = a.take<int>(p0);
+    b.kept_n = a.take<int>(1);
+    b.Fd = a.take<double>(r * p0);
+    b.Gk = a.take<double>(p0 * p0);
+    b.Yd = a.take<double>(r * p0);
+    b.Q = a.take<T>(r * p0);
+    b.Wc = a.take<T>(p0 * n);
+    return b;
+}
+
+template <typename T>
+std::vector<BlockInfo<T>> block_info(const lrr_problem* p) {
+    constexpr int B2 = 2 * jacobi_bs<T>();
+    const int rmax = (int)std::min<int64_t>(p->m, p->n);
+    std::vector<BlockInfo<T>> v((size_t)p->t);
+    for (int i = 0; i < p->t; ++i) {
+        v[i].col0 = p->offsets[i];
+        v[i].l = (int)(p->offsets[i + 1] - p->offsets[i]);
+        v[i].pmax = std::min(rmax, v[i].l);
+        v[i].ppmax = round_up(v[i].pmax, B2);
+    }
+    return v;
+}
+
+inline unsigned grid1(int64_t count, int threads = 256) {
+    return (unsigned)std::min<int64_t>((count + threads - 1) / threads, 152 * 32);
+}
+
+template <typename T>
+GemmDesc<T> gdesc(const T* A, int64_t lda, const T* B, int64_t ldb, T* C, int64_t ldc, int m, int n, int k,
+                  const int* flag, T alpha = T(1), T beta = T(0)) {
+    GemmDesc<T> d{};
+    d.A = A; d.B = B; d.C = C; d.flag = flag; d.ccol = nullptr; d.kscale = nullptr; d.absmax = nullptr;
+    d.lda = lda; d.ldb = ldb; d.ldc = ldc; d.m = m; d.n = n; d.k = k; d.alpha = alpha; d.beta = beta;
+    return d;
+}
+
+// A set of grouped-GEMM launches prepared once per solve.
+template <typename T>
+struct GemmSet {
+    int first = 0, count = 0, max_m = 0, max_n = 0;
+    bool ta = false, tb = false;
+};
+
+template <typename T, typename Tin>
+int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_bytes, lrr_result* res,
+               cudaStream_t s, bool dfc) {
+    const auto blk = block_info<T>(p);
+    const bool need_md = !std::is_same<Tin, double>::value;
+    Arena probe(nullptr);
+    carve<T>(probe, p, need_md, blk);
+    const size_t need = probe.off + kAlign;
+    void* own = nullptr;
+    if (!ws) {
+        if (cudaMallocAsync(&own, need, s) != cudaSuccess) return LRR_ERR_CUDA;
+        ws = own;
+        ws_bytes = need;
+    }
+    struct Free {
+        void* p; cudaStream_t s;
+        ~Free() { if (p) cudaFreeAsync(p, s); }
+    } guard{own, s};
+    if (ws_bytes < need - kAlign || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return LRR_ERR_WORKSPACE;
+    Arena arena(ws);
+    Buffers<T> B = carve<T>(arena, p, need_md, blk);
+    const int64_t m = p->m, n = p->n;
+    const int t = p->t;
+    const Tin* M = static_cast<const Tin*>(p->M);
+
+    cudaEvent_t ev[4];
+    for (auto& e : ev) LRR_CUDA_TRY(cudaEventCreate(&e));
+    struct EvFree {
+        cudaEvent_t* e;
+        ~EvFree() { for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]); }
+    } evguard{ev};
+    LRR_CUDA_TRY(cudaEventRecord(ev[0], s));
+
+    // ---- checks: non-finite entries
+    int hflag = 0;
+    LRR_CUDA_TRY(cudaMemsetAsync(B.flag, 0, sizeof(int) * 4, s));
+    k::nonfinite_check<Tin><<<dim3(grid1(m), (unsigned)std::min<int64_t>(n, 65535)), 256, 0, s>>>(M, p->ldm, m, n, B.flag);
+    LRR_CUDA_TRY(cudaMemcpyAsync(&hflag, B.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LRR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hflag) return LRR_ERR_NONFINITE;
+
+    // ---- D step inputs
+    std::vector<int> colblk((size_t)n);
+    for (int i = 0; i < t; ++i)
+        for (int64_t j = p->offsets[i]; j < p->offsets[i + 1]; ++j) colblk[(size_t)j] = i;
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.perm, p->perm, sizeof(int64_t) * n, cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.colblk, colblk.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+
+    // ---- one-time factor in float64
+    const double* Md = nullptr;
+    int64_t ldmd = p->ldm;
+    if (need_md) {
+        k::gather_cols<double, Tin><<<dim3(grid1(m), (unsigned)std::min<int64_t>(n, 65535)), 256, 0, s>>>(M, p->ldm, nullptr, m, n, B.Md);
+        Md = B.Md;
+        ldmd = m;
+    } else {
+        Md = reinterpret_cast<const double*>(M);
+    }
+    std::vector<GemmDesc<double>> hd(2);
+    hd[0] = gdesc<double>(Md, ldmd, Md, ldmd, B.Kd, B.mpp, (int)m, (int)m, (int)n, nullptr);
+    GemmDesc<double>* dd = reinterpret_cast<GemmDesc<double>*>(B.gd);  // scratch slot, reused below
+    LRR_CUDA_TRY(cudaMemcpyAsync(dd, hd.data(), sizeof(GemmDesc<double>), cudaMemcpyHostToDevice, s));
+    k::init_padded<double><<<grid1((int64_t)B.mpp * B.mpp), 256, 0, s>>>(B.Kd, (int)m, B.mpp, -1.0, 0);
+    k::init_padded<double><<<grid1((int64_t)B.mpp * B.mpp), 256, 0, s>>>(B.Wd, (int)m, B.mpp, 1.0, 1);
+    LRR_CUDA_TRY(gemm_grouped<double>(dd, 1, false, true, (int)m, (int)m, s));
+    {
+        // scale for the Jacobi noise floor: max diagonal of K
+        k::diag_of<double><<<ceil_div(m, 256), 256, 0, s>>>(B.Kd, B.mpp, m, B.lam_raw);
+        std::vector<double> dg((size_t)m);
+        LRR_CUDA_TRY(cudaMemcpyAsync(dg.data(), B.lam_raw, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+        LRR_CUDA_TRY(cudaStreamSynchronize(s));
+        double sc = 0;
+        for (double v : dg) sc = std::max(sc, std::fabs(v));
+        if (!(sc > 0)) return LRR_ERR_RANK;
+        JacDesc<double> jd{};
+        jd.G = B.Kd; jd.W = B.Wd; jd.R = B.Rd; jd.done = B.jac_done_d; jd.off = B.jac_off_d;
+        jd.active = nullptr; jd.scale = B.jac_scale_d; jd.pp = B.mpp;
+        LRR_CUDA_TRY(cudaMemcpyAsync(B.jac_scale_d, &sc, sizeof(double), cudaMemcpyHostToDevice, s));
+        LRR_CUDA_TRY(cudaMemcpyAsync(B.jac_setup, &jd, sizeof(jd), cudaMemcpyHostToDevice, s));
+        LRR_CUDA_TRY(jacobi_sweeps<double>(B.jac_setup, 1, B.mpp, 40, 1e-13, s));
+    }
+    k::diag_of<double><<<ceil_div(m, 256), 256, 0, s>>>(B.Kd, B.mpp, m, B.lam_raw);
+    std::vector<double> ev_h((size_t)m);
+    LRR_CUDA_TRY(cudaMemcpyAsync(ev_h.data(), B.lam_raw, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    LRR_CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<int> order((size_t)m);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ev_h[a] > ev_h[b]; });
+    const double smax = std::sqrt(std::max(ev_h[order[0]], 0.0));
+    const double rtol = o->rank_tol > 0 ? o->rank_tol : 1e-6;
+    int r = 0;
+    while (r < (int)m && r < B.rmax && std::sqrt(std::max(ev_h[order[r]], 0.0)) > rtol * smax) ++r;
+    if (r == 0 || !(smax > 0)) return LRR_ERR_RANK;
+    std::vector<double> lam_sorted((size_t)r);
+    for (int k2 = 0; k2 < r; ++k2) lam_sorted[k2] = ev_h[order[k2]];
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.order, order.data(), sizeof(int) * r, cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.lam, lam_sorted.data(), sizeof(double) * r, cudaMemcpyHostToDevice, s));
+    k::setup_factors<<<dim3(grid1(m), (unsigned)r), 256, 0, s>>>(B.Wd, B.mpp, m, r, B.order, B.lam, B.Ud, B.Usd);
+    k::setup_scalars<T><<<dim3(grid1(m), (unsigned)r), 256, 0, s>>>(B.lam, r, B.Ud, m, B.sig, B.dinv, B.U, B.US);
+    hd[1] = gdesc<double>(Md, ldmd, B.Usd, m, B.Vd, n, (int)n, r, (int)m, nullptr);
+    LRR_CUDA_TRY(cudaMemcpyAsync(dd + 1, &hd[1], sizeof(GemmDesc<double>), cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(gemm_grouped<double>(dd + 1, 1, true, false, (int)n, r, s));
+    k::copy_convert_f64<T><<<grid1(n * r), 256, 0, s>>>(B.Vd, B.V, n * r);
+    LRR_CUDA_TRY(cudaMemsetAsync(B.nu, 0, sizeof(T), s));
+    k::row_norm_max<T><<<ceil_div(n, 256), 256, 0, s>>>(B.V, n, r, B.nu);
+    T nu_h = T(0);
+    LRR_CUDA_TRY(cudaMemcpyAsync(&nu_h, B.nu, sizeof(T), cudaMemcpyDeviceToHost, s));
+    LRR_CUDA_TRY(cudaStreamSynchronize(s));
+    LRR_CUDA_TRY(cudaEventRecord(ev[1], s));
+
+    // ---- per-block tables (sizes now known: p_i = min(r, l_i))
+    constexpr int B2 = 2 * jacobi_bs<T>();
+    std::vector<int> pv((size_t)t), ppv((size_t)t);
+    std::vector<char> tall((size_t)t);
+    int max_p = 0, max_pp = 0, max_l = 0;
+    for (int i = 0; i < t; ++i) {
+        tall[i] = blk[i].l <= r;
+        pv[i] = std::min(r, blk[i].l);
+        ppv[i] = round_up(pv[i], B2);
+        max_p = std::max(max_p, pv[i]);
+        max_pp = std::max(max_pp, ppv[i]);
+        max_l = std::max(max_l, blk[i].l);
+    }
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.Gp, B.G.data(), sizeof(T*) * t, cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.hp, B.h.data(), sizeof(T*) * t, cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.pv, pv.data(), sizeof(int) * t, cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.ppv, ppv.data(), sizeof(int) * t, cudaMemcpyHostToDevice, s));
+    std::vector<JacDesc<T>> jdh((size_t)t);
+    for (int i = 0; i < t; ++i) {
+        JacDesc<T>& j = jdh[i];
+        j.G = B.G[i]; j.W = B.W[i]; j.R = B.R[i]; j.done = B.jdone + i; j.off = B.joff + i;
+        j.active = B.svt_on + i; j.scale = B.jscale + i; j.pp = ppv[i];
+    }
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.jd, jdh.data(), sizeof(JacDesc<T>) * t, cudaMemcpyHostToDevice, s));
+
+    // grouped GEMM descriptor sets
+    std::vector<GemmDesc<T>> gh;
+    std::vector<GemmSet<T>> sets;
+    auto add_set = [&](bool ta, bool tb, const std::vector<GemmDesc<T>>& ds) {
+        GemmSet<T> g;
+        g.first = (int)gh.size(); g.count = (int)ds.size(); g.ta = ta; g.tb = tb;
+        for (auto& d : ds) { g.max_m = std::max(g.max_m, d.m); g.max_n = std::max(g.max_n, d.n); gh.push_back(d); }
+        sets.push_back(g);
+        return (int)sets.size() - 1;
+    };
+    std::vector<GemmDesc<T>> gram_tall, gram_wide, warm1, warm2, hmat, j_tall, j_wide, tmul, mzmul, exact;
+    for (int i = 0; i < t; ++i) {
+        const int64_t c0 = blk[i].col0;
+        const int l = blk[i].l, pp_ = ppv[i], pi = pv[i];
+        T* Ai = B.A + c0 * r;
+        if (tall[i]) {
+            gram_tall.push_back(gdesc<T>(Ai, r, Ai, r, B.G[i], pp_, l, l, r, B.act + i));
+            j_tall.push_back(gdesc<T>(Ai, r, B.H[i], pp_, B.Jt + c0 * r, r, r, l, l, B.act + i));
+        } else {
+            gram_wide.push_back(gdesc<T>(Ai, r, Ai, r, B.G[i], pp_, r, r, l, B.act + i));
+            j_wide.push_back(gdesc<T>(B.H[i], pp_, Ai, r, B.Jt + c0 * r, r, r, l, r, B.act + i));
+        }
+        warm1.push_back(gdesc<T>(B.G[i], pp_, B.W[i], pp_, B.T1[i], pp_, pi, pi, pi, B.svt_on + i));
+        warm2.push_back(gdesc<T>(B.W[i], pp_, B.T1[i], pp_, B.G[i], pp_, pi, pi, pi, B.svt_on + i));
+        GemmDesc<T> hm = gdesc<T>(B.W[i], pp_, B.W[i], pp_, B.H[i], pp_, pi, pi, pi, B.act + i);
+        hm.kscale = B.h[i];
+        hmat.push_back(hm);
+        tmul.push_back(gdesc<T>(B.U, m, B.P + c0 * m, m, B.Tt + c0 * r, r, r, l, (int)m, B.act + i));
+        mzmul.push_back(gdesc<T>(B.US, m, B.Zt + c0 * r, r, B.MZ + c0 * m, m, (int)m, l, r, B.act + i));
+        GemmDesc<T> ex = gdesc<T>(B.V, n, B.D + c0 * r, r, nullptr, 0, (int)n, l, r, B.need_exact + i);
+        ex.absmax = B.r2x + i;
+        exact.push_back(ex);
+    }
+    const int S_GT = gram_tall.empty() ? -1 : add_set(true, false, gram_tall);
+    const int S_GW = gram_wide.empty() ? -1 : add_set(false, true, gram_wide);
+    const int S_W1 = add_set(false, false, warm1);
+    const int S_W2 = add_set(true, false, warm2);
+    const int S_H = add_set(false, true, hmat);
+    const int S_JT = j_tall.empty() ? -1 : add_set(false, false, j_tall);
+    const int S_JW = j_wide.empty() ? -1 : add_set(false, false, j_wide);
+    const int S_T = add_set(true, false, tmul);
+    const int S_MZ = add_set(false, false, mzmul);
+    const int S_EX = add_set(false, false, exact);
+    if (gh.size() > 16 * (size_t)t + 16) return LRR_ERR_INVALID;
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.gd, gh.data(), sizeof(GemmDesc<T>) * gh.size(), cudaMemcpyHostToDevice, s));
+    auto run_set = [&](int si) -> cudaError_t {
+        if (si < 0) return cudaSuccess;
+        const GemmSet<T>& g = sets[si];
+        return gemm_grouped<T>(B.gd + g.first, g.count, g.ta, g.tb, g.max_m, g.max_n, s);
+    };
+
+    // ---- state
+    k::gather_cols<T, Tin><<<dim3(grid1(m), (unsigned)std::min<int64_t>(n, 65535)), 256, 0, s>>>(M, p->ldm, B.perm, m, n, B.C);
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.P, B.C, sizeof(T) * m * n, cudaMemcpyDeviceToDevice, s));
+    LRR_CUDA_TRY(cudaMemsetAsync(B.E, 0, sizeof(T) * m * n, s));
+    LRR_CUDA_TRY(cudaMemsetAsync(B.Y1, 0, sizeof(T) * m * n, s));
+    {
+        T* zs[5] = {B.Zt, B.Jt, B.Y2t, B.A, B.D};
+        for (T* x : zs) { LRR_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * r * n, s)); }
+    }
+    for (int i = 0; i < t; ++i) {
+        k::init_padded<T><<<grid1((int64_t)ppv[i] * ppv[i]), 256, 0, s>>>(B.G[i], pv[i], ppv[i], T(-1), 0);
+        k::init_padded<T><<<grid1((int64_t)ppv[i] * ppv[i]), 256, 0, s>>>(B.W[i], pv[i], ppv[i], T(1), 1);
+    }
+    std::vector<double> mu0((size_t)t, o->mu0);
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.mu, mu0.data(), sizeof(double) * t, cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.mu_fin, mu0.data(), sizeof(double) * t, cudaMemcpyHostToDevice, s));
+    {
+        int* zi[7] = {B.iters, B.conv, B.rank_cur, B.rank_fin, B.svt_on, B.need_exact, B.conv_bound};
+        for (int* x : zi) { LRR_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(int) * t, s)); }
+        T* zt[3] = {B.r1, B.dmax, B.r2x};
+        for (T* x : zt) { LRR_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * t, s)); }
+    }
+    LRR_CUDA_TRY(cudaMemsetAsync(B.resid, 0, sizeof(double) * 2 * t, s));
+
+    const int sweeps = o->jacobi_sweeps > 0 ? o->jacobi_sweeps : 12;
+    const T jtol = sizeof(T) == 8 ? T(1e-13) : T(4e-6);
+    const unsigned wgrid_n = (unsigned)((n * 32 + 255) / 256);
+    auto iteration = [&]() -> int {
+        // J-step: SVT of A = Zt + Y2t/mu through the Gram eigendecomposition
+        LRR_CUDA_TRY(run_set(S_GT));
+        LRR_CUDA_TRY(run_set(S_GW));
+        k::svt_gate<T><<<t, 256, 0, s>>>(B.Gp, B.pv, B.ppv, B.act, B.mu, B.svt_on, B.jscale, t);
+        LRR_CUDA_TRY(run_set(S_W1));
+        LRR_CUDA_TRY(run_set(S_W2));
+        LRR_CUDA_TRY(jacobi_sweeps<T>(B.jd, t, max_pp, sweeps, jtol, s));
+        k::svt_weights<T><<<t, 256, 0, s>>>(B.Gp, B.hp, B.pv, B.ppv, B.act, B.svt_on, B.mu, B.rank_cur, t);
+        LRR_CUDA_TRY(run_set(S_H));
+        LRR_CUDA_TRY(run_set(S_JT));
+        LRR_CUDA_TRY(run_set(S_JW));
+        // Z-step
+        LRR_CUDA_TRY(run_set(S_T));
+        k::z_update<T><<<wgrid_n, 256, 0, s>>>(r, n, B.colblk, B.act, B.mu, o->rho, o->mu_max, B.Tt, B.Jt, B.Y2t,
+                                               B.Zt, B.D, B.A, B.sig, B.dinv, B.dmax);
+        // E-step, residuals, duals
+        LRR_CUDA_TRY(run_set(S_MZ));
+        k::e_update<T><<<wgrid_n, 256, 0, s>>>(m, n, B.colblk, B.act, B.mu, o->rho, o->mu_max, o->lambda, B.C,
+                                               B.MZ, B.Y1, B.E, B.P, B.r1);
+        k::stop_part1<T><<<ceil_div(t, 128), 128, 0, s>>>(t, B.act, B.r1, B.dmax, nu_h, o->eps, B.need_exact,
+                                                          B.conv_bound);
+        LRR_CUDA_TRY(run_set(S_EX));
+        k::stop_part2<T><<<ceil_div(t, 128), 128, 0, s>>>(t, B.act, B.iters, B.mu, o->rho, o->mu_max, o->eps,
+                                                          o->max_iter, B.r1, B.dmax, B.r2x, B.need_exact,
+                                                          B.conv_bound, nu_h, B.resid, B.rank_cur, B.rank_fin,
+                                                          B.conv, B.mu_fin);
+        LRR_CUDA_TRY(cudaGetLastError());
+        return LRR_OK;
+    };
+    auto run_loop = [&](const std::vector<int>& act0) -> int {
+        LRR_CUDA_TRY(cudaMemcpyAsync(B.act, act0.data(), sizeof(int) * t, cudaMemcpyHostToDevice, s));
+        std::vector<int> ah((size_t)t);
+        int done_it = 0;
+        const int chunk = 4;
+        while (done_it < o->max_iter) {
+            for (int c = 0; c < chunk && done_it < o->max_iter; ++c, ++done_it) {
+                const int rc = iteration();
+                if (rc != LRR_OK) return rc;
+            }
+            LRR_CUDA_TRY(cudaMemcpyAsync(ah.data(), B.act, sizeof(int) * t, cudaMemcpyDeviceToHost, s));
+            LRR_CUDA_TRY(cudaStreamSynchronize(s));
+            if (std::none_of(ah.begin(), ah.end(), [](int v) { return v != 0; })) break;
+        }
+        return LRR_OK;
+    };
+    if (o->batched) {
+        const int rc = run_loop(std::vector<int>((size_t)t, 1));
+        if (rc != LRR_OK) return rc;
+    } else {
+        for (int i = 0; i < t; ++i) {
+            std::vector<int> a0((size_t)t, 0);
+            a0[i] = 1;
+            const int rc = run_loop(a0);
+            if (rc != LRR_OK) return rc;
+        }
+    }
+    LRR_CUDA_TRY(cudaEventRecord(ev[2], s));
+
+    // ---- C step
+    int k1 = 0;
+    std::vector<int> rank_fin((size_t)t);
+    LRR_CUDA_TRY(cudaMemcpyAsync(rank_fin.data(), B.rank_fin, sizeof(int) * t, cudaMemcpyDeviceToHost, s));
+    T* Zfinal = B.Zt;
+    if (dfc && t > 1) {
+        const int p0 = pv[0], pp0 = ppv[0];
+        // keep-list of block 1's SVT directions with h > 0 (final iteration)
+        k::kept_columns<T><<<1, 32, 0, s>>>(B.h[0], p0, B.kept, B.kept_n);
+        const T* src;
+        int64_t ldsrc;
+        if (tall[0]) {
+            // left factor of J_1 = A W h W^T:  J_1 W = (A W) h  -> columns with h > 0
+            std::vector<GemmDesc<T>> fd{gdesc<T>(B.Jt, r, B.W[0], pp0, B.Tt, r, r, p0, p0, nullptr)};
+            LRR_CUDA_TRY(cudaMemcpyAsync(B.gd + gh.size(), fd.data(), sizeof(GemmDesc<T>), cudaMemcpyHostToDevice, s));
+            LRR_CUDA_TRY(gemm_grouped<T>(B.gd + gh.size(), 1, false, false, r, p0, s));
+            src = B.Tt;
+            ldsrc = r;
+        } else {
+            // J_1 = W h W^T A: column space spanned by the kept eigenvectors
+            src = B.W[0];
+            ldsrc = pp0;
+        }
+        k::gather_normalise_f64<T><<<p0, 256, 0, s>>>(src, ldsrc, r, B.kept, B.kept_n, B.Fd);
+        LRR_CUDA_TRY(cudaMemcpyAsync(&k1, B.kept_n, sizeof(int), cudaMemcpyDeviceToHost, s));
+        LRR_CUDA_TRY(cudaStreamSynchronize(s));
+        if (k1 > 0) {
+            // orthonormal basis of span(F) in float64: the columns are already
+            // orthogonal up to the Jacobi tolerance, so Newton-Schulz steps
+            // X <- X (3I - X^T X)/2 converge quadratically to the polar factor
+            GemmDesc<double>* d64 = reinterpret_cast<GemmDesc<double>*>(B.gd + gh.size());
+            std::vector<GemmDesc<double>> nd{gdesc<double>(B.Fd, r, B.Fd, r, B.Gk, k1, k1, k1, r, nullptr),
+                                             gdesc<double>(B.Fd, r, B.Gk, k1, B.Yd, r, r, k1, k1, nullptr)};
+            LRR_CUDA_TRY(cudaMemcpyAsync(d64, nd.data(), sizeof(GemmDesc<double>) * 2, cudaMemcpyHostToDevice, s));
+            for (int it = 0; it < 3; ++it) {
+                LRR_CUDA_TRY(gemm_grouped<double>(d64, 1, true, false, k1, k1, s));
+                LRR_CUDA_TRY(gemm_grouped<double>(d64 + 1, 1, false, false, r, k1, s));
+                k::ns_combine<<<grid1((int64_t)r * k1), 256, 0, s>>>(B.Fd, B.Yd, (int64_t)r * k1);
+            }
+            k::copy_convert_f64<T><<<grid1((int64_t)r * k1), 256, 0, s>>>(B.Fd, B.Q, (int64_t)r * k1);
+            std::vector<GemmDesc<T>> cd{gdesc<T>(B.Q, r, B.Zt, r, B.Wc, k1, k1, (int)n, r, nullptr),
+                                        gdesc<T>(B.Q, r, B.Wc, k1, B.Tt, r, r, (int)n, k1, nullptr)};
+            GemmDesc<T>* dT = B.gd + gh.size() + 4;
+            LRR_CUDA_TRY(cudaMemcpyAsync(dT, cd.data(), sizeof(GemmDesc<T>) * 2, cudaMemcpyHostToDevice, s));
+            LRR_CUDA_TRY(gemm_grouped<T>(dT, 1, true, false, k1, (int)n, s));
+            LRR_CUDA_TRY(gemm_grouped<T>(dT + 1, 1, false, false, r, (int)n, s));
+        } else {
+            LRR_CUDA_TRY(cudaMemsetAsync(B.Tt, 0, sizeof(T) * r * n, s));
+        }
+        Zfinal = B.Tt;
+    } else {
+        k1 = rank_fin[0];
+    }
+    if (res && res->Z) {
+        GemmDesc<T> zd = gdesc<T>(B.V, n, Zfinal, r, static_cast<T*>(res->Z), n, (int)n, (int)n, r, nullptr);
+        zd.ccol = B.perm;
+        GemmDesc<T>* dz = B.gd + gh.size() + 8;
+        LRR_CUDA_TRY(cudaMemcpyAsync(dz, &zd, sizeof(zd), cudaMemcpyHostToDevice, s));
+        LRR_CUDA_TRY(gemm_grouped<T>(dz, 1, false, false, (int)n, (int)n, s));
+    }
+    if (res && res->S)
+        k::scatter_cols<T><<<dim3(grid1(m), (unsigned)std::min<int64_t>(n, 65535)), 256, 0, s>>>(B.E, m, n, B.perm, static_cast<T*>(res->S));
+    LRR_CUDA_TRY(cudaEventRecord(ev[3], s));
+
+    std::vector<int> iters_h((size_t)t), conv_h((size_t)t);
+    std::vector<double> resid_h((size_t)2 * t);
+    LRR_CUDA_TRY(cudaMemcpyAsync(iters_h.data(), B.iters, sizeof(int) * t, cudaMemcpyDeviceToHost, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(conv_h.data(), B.conv, sizeof(int) * t, cudaMemcpyDeviceToHost, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(resid_h.data(), B.resid, sizeof(double) * 2 * t, cudaMemcpyDeviceToHost, s));
+    LRR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (res) {
+        if (res->iters) std::copy(iters_h.begin(), iters_h.end(), res->iters);
+        if (res->resid) std::copy(resid_h.begin(), resid_h.end(), res->resid);
+        if (res->ranks) {
+            res->ranks[0] = r;
+            res->ranks[1] = k1;
+            for (int i = 0; i < t; ++i) res->ranks[2 + i] = rank_fin[i];
+        }
+        if (res->timings_ms) {
+            float a = 0, b2 = 0, c = 0;
+            cudaEventElapsedTime(&a, ev[0], ev[1]);
+            cudaEventElapsedTime(&b2, ev[1], ev[2]);
+            cudaEventElapsedTime(&c, ev[2], ev[3]);
+            res->timings_ms[0] = a; res->timings_ms[1] = b2; res->timings_ms[2] = c;
+        }
+    }
+    for (int i = 0; i < t; ++i)
+        if (!conv_h[i]) return LRR_NOT_CONVERGED;
+    return LRR_OK;
+}
+
+template <typename T, typename Tin>
+size_t workspace_impl(const lrr_problem* p) {
+    const auto blk = block_info<T>(p);
+    Arena probe(nullptr);
+    carve<T>(probe, p, !std::is_same<Tin, double>::value, blk);
+    return probe.off + kAlign;
+}
+
+int dispatch(const lrr_problem* p, const lrr_options* o, void* ws, size_t wsb, lrr_result* r, void* stream, bool dfc) {
+    if (!valid_problem(p, o)) return LRR_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    switch (o->precision) {
+        case LRR_PREC_F64: return solve_impl<double, double>(p, o, ws, wsb, r, s, dfc);
+        case LRR_PREC_F32: return solve_impl<float, float>(p, o, ws, wsb, r, s, dfc);
+        default: return LRR_ERR_UNSUPPORTED;
+    }
+}
+
+}  // namespace
+}  // namespace lrr
+
+extern "C" {
+
+size_t lrr_workspace_bytes(const lrr_problem* p, const lrr_options* o) {
+    if (!lrr::valid_problem(p, o)) return 0;
+    switch (o->precision) {
+        case LRR_PREC_F64: return lrr::workspace_impl<double, double>(p);
+        case LRR_PREC_F32: return lrr::workspace_impl<float, float>(p);
+        default: return 0;
+    }
+}
+
+int lrr_solve(const lrr_problem* p, const lrr_options* o, void* ws, size_t wsb, lrr_result* r, void* stream) {
+    if (!p || p->t != 1) return LRR_ERR_INVALID;
+    return lrr::dispatch(p, o, ws, wsb, r, stream, false);
+}
+
+int dfc_lrr_solve(const lrr_problem* p, const lrr_options* o, void* ws, size_t wsb, lrr_result* r, void* stream) {
+    return lrr::dispatch(p, o, ws, wsb, r, stream, true);
+}
+
+void lrr_default_options(lrr_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->lambda = 0.1;
+    o->rho = 1.1;
+    o->mu0 = 1e-6;
+    o->mu_max = 1e10;
+    o->eps = 1e-6;
+    o->max_iter = 1000;
+    o->precision = LRR_PREC_F32;
+    o->batched = 1;
+    o->jacobi_sweeps = 0;
+    o->rank_tol = 0.0;
+    o->mixed_switch = 0.0;
+}
+
+const char* lrr_status_string(int s) {
+    switch (s) {
+        case LRR_OK: return "ok";
+        case LRR_NOT_CONVERGED: return "not converged: at least one block reached max_iter";
+        case LRR_ERR_INVALID: return "invalid argument";
+        case LRR_ERR_NONFINITE: return "M contains NaN or Inf";
+        case LRR_ERR_CUDA: return "CUDA runtime error";
+        case LRR_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
+        case LRR_ERR_RANK: return "M is numerically zero";
+        case LRR_ERR_UNSUPPORTED: return "precision mode not available";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -86,7 +86,33 @@ typedef struct {
     double rank_tol;            /* rank(M) = #{sigma > rank_tol * sigma_max} (0 -> 1e-6)  */
     double mixed_switch;        /* MIXED: leave bf16 once the primal residual is below
                                    this (0 -> 1e-3)                                      */
+    int32_t profile;            /* 1: record per-phase CUDA-event times into stats     */
 } lrr_options;
+
+/* Per-phase device time of one solve, measured with CUDA events recorded on
+ * the solve's stream around each phase (only when lrr_options.profile != 0),
+ * and kernel-launch counts (always). */
+#define LRR_NPHASE 12
+enum {
+    LRR_PH_SETUP = 0,       /* checks, M M^T, its eigendecomposition, V          */
+    LRR_PH_GRAM = 1,        /* SVT Gram products A^T A / A A^T                    */
+    LRR_PH_WARM = 2,        /* warm start W^T G W                                 */
+    LRR_PH_JACOBI = 3,      /* block-Jacobi sweeps                                */
+    LRR_PH_SVT_APPLY = 4,   /* H = W h W^T and J = A H (or H A), gate, weights   */
+    LRR_PH_ZGEMM = 5,       /* U^T P                                              */
+    LRR_PH_ZUPDATE = 6,     /* Z-step, Y2 step, next SVT input                    */
+    LRR_PH_MZGEMM = 7,      /* U diag(sigma) Z                                    */
+    LRR_PH_EUPDATE = 8,     /* E-step, Y1 step, residual                          */
+    LRR_PH_STOP = 9,        /* stop test incl. exact ||Z-J||_inf products         */
+    LRR_PH_COMBINE = 10,    /* C step and output scatter                          */
+    LRR_PH_HOST = 11        /* host synchronisation points (flag read-back)       */
+};
+typedef struct {
+    double phase_ms[LRR_NPHASE];
+    int64_t phase_launches[LRR_NPHASE];
+    int64_t launches;           /* kernels launched by the call                       */
+    int64_t iterations;         /* ALM iterations launched (all blocks together)      */
+} lrr_stats;
 
 typedef struct {
     void* Z;                    /* (device, may be NULL) n x n, ld n, original column
@@ -98,6 +124,7 @@ typedef struct {
     int32_t* ranks;             /* (host, may be NULL) t+2: [rank(M), k1, SVT rank of each
                                    block at its final iteration]                          */
     double* timings_ms;         /* (host, may be NULL) 3: setup, iteration, combine        */
+    lrr_stats* stats;           /* (host, may be NULL) per-phase times and launch counts  */
 } lrr_result;
 
 /* Bytes of device workspace a solve of `p` with options `o` needs (0 on invalid
@@ -114,6 +141,19 @@ LRR_API int lrr_solve(const lrr_problem* p, const lrr_options* o, void* workspac
  * where it is the identity).  Returns an lrr_status. */
 LRR_API int dfc_lrr_solve(const lrr_problem* p, const lrr_options* o, void* workspace, size_t workspace_bytes,
                   lrr_result* r, void* stream);
+
+/* Singular-value thresholding, the proximal map of tau ||.||_* that forms the
+ * J-step of every ALM iteration: for A = U diag(s) V^T,
+ *   J = U diag(max(s - tau, 0)) V^T.
+ * A (device, rows x cols, ld lda) and J (device, rows x cols, ld ldj) are
+ * column-major float (precision LRR_PREC_F32) or double (LRR_PREC_F64); J may
+ * not alias A.  *rank (host, may be NULL) receives #{s > tau}.  Computed as in
+ * the solver: one-sided block Jacobi on the columns of A (tall) or A^T (wide),
+ * from a cold start.  Scratch memory is taken with cudaMallocAsync on `stream`
+ * and released before returning; the call synchronises `stream`.
+ * rows, cols <= 65536. */
+LRR_API int lrr_svt(const void* A, int64_t rows, int64_t cols, int64_t lda, double tau, void* J, int64_t ldj,
+                    int32_t precision, int32_t* rank, void* stream);
 
 /* Fill `o` with the defaults above (lambda = 0.1). */
 LRR_API void lrr_default_options(lrr_options* o);

@@ -21,7 +21,7 @@ LRR_PREC_F64, LRR_PREC_F32, LRR_PREC_MIXED = 0, 1, 2
 PRECISIONS = {"f64": LRR_PREC_F64, "f32": LRR_PREC_F32, "mixed": LRR_PREC_MIXED}
 
 # every symbol include/dfc_lrr.h declares
-EXPORTS = ("lrr_workspace_bytes", "lrr_solve", "dfc_lrr_solve", "lrr_default_options", "lrr_status_string")
+EXPORTS = ("lrr_workspace_bytes", "lrr_solve", "dfc_lrr_solve", "lrr_svt", "lrr_default_options", "lrr_status_string")
 
 
 class LrrProblem(ctypes.Structure):
@@ -34,13 +34,22 @@ class LrrOptions(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("rho", ctypes.c_double), ("mu0", ctypes.c_double),
                 ("mu_max", ctypes.c_double), ("eps", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("batched", ctypes.c_int32), ("jacobi_sweeps", ctypes.c_int32),
-                ("rank_tol", ctypes.c_double), ("mixed_switch", ctypes.c_double)]
+                ("rank_tol", ctypes.c_double), ("mixed_switch", ctypes.c_double), ("profile", ctypes.c_int32)]
+
+NPHASE = 12
+PHASES = ("setup", "gram", "warm", "jacobi", "svt_apply", "zgemm", "zupdate", "mzgemm", "eupdate", "stop",
+          "combine", "host")
+
+
+class LrrStats(ctypes.Structure):
+    _fields_ = [("phase_ms", ctypes.c_double * NPHASE), ("phase_launches", ctypes.c_int64 * NPHASE),
+                ("launches", ctypes.c_int64), ("iterations", ctypes.c_int64)]
 
 
 class LrrResult(ctypes.Structure):
     _fields_ = [("Z", ctypes.c_void_p), ("S", ctypes.c_void_p), ("iters", ctypes.POINTER(ctypes.c_int32)),
                 ("resid", ctypes.POINTER(ctypes.c_double)), ("ranks", ctypes.POINTER(ctypes.c_int32)),
-                ("timings_ms", ctypes.POINTER(ctypes.c_double))]
+                ("timings_ms", ctypes.POINTER(ctypes.c_double)), ("stats", ctypes.POINTER(LrrStats))]
 
 
 _LIB = None
@@ -60,6 +69,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         fn.restype = ctypes.c_int
         fn.argtypes = [ctypes.POINTER(LrrProblem), ctypes.POINTER(LrrOptions), ctypes.c_void_p, ctypes.c_size_t,
                        ctypes.POINTER(LrrResult), ctypes.c_void_p]
+    lib.lrr_svt.restype = ctypes.c_int
+    lib.lrr_svt.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                            ctypes.c_void_p]
     lib.lrr_default_options.restype = None
     lib.lrr_default_options.argtypes = [ctypes.POINTER(LrrOptions)]
     lib.lrr_status_string.restype = ctypes.c_char_p
@@ -89,6 +102,7 @@ class SolveResult:
     block_ranks: np.ndarray
     timings_ms: np.ndarray
     status: int
+    stats: dict
 
 
 def column_major(x):
@@ -100,12 +114,13 @@ def column_major(x):
 
 def options(lam: float, rho: float = 1.1, mu0: float = 1e-6, mu_max: float = 1e10, eps: float = 1e-6,
             max_iter: int = 1000, precision: str = "f32", batched: bool = True, jacobi_sweeps: int = 0,
-            rank_tol: float = 0.0, mixed_switch: float = 0.0) -> LrrOptions:
+            rank_tol: float = 0.0, mixed_switch: float = 0.0, profile: bool = False) -> LrrOptions:
     o = LrrOptions()
     load().lrr_default_options(ctypes.byref(o))
     o.lambda_, o.rho, o.mu0, o.mu_max, o.eps = lam, rho, mu0, mu_max, eps
     o.max_iter, o.precision, o.batched = int(max_iter), PRECISIONS[precision], int(bool(batched))
     o.jacobi_sweeps, o.rank_tol, o.mixed_switch = int(jacobi_sweeps), float(rank_tol), float(mixed_switch)
+    o.profile = int(bool(profile))
     return o
 
 
@@ -141,7 +156,7 @@ def _solve(entry: str, M, perm, offsets, opts: LrrOptions, want_Z=True, want_S=T
         if raise_on_error:
             raise LrrError(-1)
         return SolveResult(Z=None, S=None, iters=np.zeros(t, np.int32), resid=np.zeros((t, 2)), rank_M=0, k1=0,
-                           block_ranks=np.zeros(t, np.int32), timings_ms=np.zeros(3), status=-1)
+                           block_ranks=np.zeros(t, np.int32), timings_ms=np.zeros(3), status=-1, stats={})
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=M.device)
     Z = torch.empty((n, n), dtype=M.dtype, device=M.device).t() if want_Z else None
@@ -157,13 +172,18 @@ def _solve(entry: str, M, perm, offsets, opts: LrrOptions, want_Z=True, want_S=T
     r.resid = resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     r.ranks = ranks.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     r.timings_ms = tim.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    st = LrrStats()
+    r.stats = ctypes.pointer(st)
     stream = torch.cuda.current_stream(M.device).cuda_stream
     code = getattr(lib, entry)(ctypes.byref(p), ctypes.byref(opts), ctypes.c_void_p(workspace.data_ptr()),
                                ctypes.c_size_t(workspace.numel()), ctypes.byref(r), ctypes.c_void_p(stream))
     if code < 0 and raise_on_error:
         raise LrrError(code)
     return SolveResult(Z=Z, S=S, iters=iters, resid=resid, rank_M=int(ranks[0]), k1=int(ranks[1]),
-                       block_ranks=ranks[2:].copy(), timings_ms=tim, status=int(code))
+                       block_ranks=ranks[2:].copy(), timings_ms=tim, status=int(code),
+                       stats={"phase_ms": dict(zip(PHASES, list(st.phase_ms))),
+                              "phase_launches": dict(zip(PHASES, list(st.phase_launches))),
+                              "launches": int(st.launches), "iterations": int(st.iterations)})
 
 
 def dfc_lrr_solve(M, perm, offsets, opts: LrrOptions, **kw) -> SolveResult:
@@ -175,3 +195,19 @@ def lrr_solve(M, perm, opts: LrrOptions, **kw) -> SolveResult:
     """Eq. (1) through the C ABI: one block holding every column in `perm` order."""
     n = M.shape[1]
     return _solve("lrr_solve", M, perm, np.array([0, n], np.int64), opts, **kw)
+
+
+def svt(A, tau: float):
+    """Singular-value thresholding through the C ABI: returns (J, rank)."""
+    import torch
+    lib = load()
+    A = column_major(A)
+    rows, cols = A.shape
+    J = torch.empty((cols, rows), dtype=A.dtype, device=A.device).t()
+    prec = LRR_PREC_F64 if A.dtype == torch.float64 else LRR_PREC_F32
+    rk = ctypes.c_int32(0)
+    code = lib.lrr_svt(ctypes.c_void_p(A.data_ptr()), rows, cols, A.stride(1), float(tau), ctypes.c_void_p(J.data_ptr()),
+                       J.stride(1), prec, ctypes.byref(rk), ctypes.c_void_p(torch.cuda.current_stream(A.device).cuda_stream))
+    if code < 0:
+        raise LrrError(code)
+    return J, int(rk.value)

@@ -11,6 +11,7 @@
 // E, Y1 and the residual C - M Z - E stay in the m-dimensional data space.
 #pragma once
 #include "common.cuh"
+#include "kernels.cuh"
 
 namespace lrr {
 namespace k {
@@ -69,80 +70,86 @@ __global__ void init_padded(T* __restrict__ G, int p, int pp, T diag, int eye) {
     }
 }
 
-// Per-block SVT gate: trace(G) <= tau^2 means every eigenvalue of the Gram is
-// <= tau^2, so the threshold removes all singular values and J = 0 without
-// an eigendecomposition.  Also records max |G_ii| (the Jacobi noise floor).
+// Per-block SVT gate: ||A||_F^2 <= tau^2 means every singular value of A is
+// <= tau, so the threshold removes all of them and J = 0 with no SVD.
+// The Z-step kernel of the same iteration then accumulates the next value.
 template <typename T>
-__global__ void svt_gate(T* const* __restrict__ G, const int* __restrict__ p, const int* __restrict__ pp,
-                         const int* __restrict__ act, const double* __restrict__ mu, int* __restrict__ svt_on,
-                         T* __restrict__ scale, int nblk) {
-    const int b = blockIdx.x;
+__global__ void svt_gate(const int* __restrict__ act, double* __restrict__ afro, const double* __restrict__ mu,
+                         int* __restrict__ svt_on, T* __restrict__ scale, int nblk) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nblk) return;
-    if (!act[b]) {
-        if (threadIdx.x == 0) svt_on[b] = 0;
-        return;
+    const double tau = 1.0 / mu[b];
+    svt_on[b] = (act[b] && afro[b] > tau * tau) ? 1 : 0;
+    if (act[b]) {
+        scale[b] = (T)afro[b];
+        afro[b] = 0.0;
     }
-    const T* g = G[b];
-    const int n = p[b], ld = pp[b];
-    double tr = 0.0;
+}
+
+// Largest squared column norm of X (the Jacobi noise scale): one CTA per block.
+template <typename T>
+__global__ void col_norm_max(const OsjDesc<T>* __restrict__ descs, const int* __restrict__ on, T* __restrict__ scale,
+                             int nblk) {
+    const int b = blockIdx.x;
+    if (b >= nblk || !on[b]) return;
+    const OsjDesc<T> d = descs[b];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     T mx = T(0);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const T v = g[i + (int64_t)i * ld];
-        tr += (double)v;
-        mx = fmax(mx, fabs(v));
+    for (int j = warp; j < d.p; j += nw) {
+        const T* x = d.X + (int64_t)j * d.ldx;
+        T acc = T(0);
+        for (int i = lane; i < d.L; i += 32) acc += x[i] * x[i];
+        mx = fmax(mx, warp_sum(acc));
     }
-    __shared__ double s_tr[32];
-    __shared__ T s_mx[32];
-    tr = warp_sum(tr);
-    mx = warp_max(mx);
-    if ((threadIdx.x & 31) == 0) { s_tr[threadIdx.x >> 5] = tr; s_mx[threadIdx.x >> 5] = mx; }
+    __shared__ T s_m[32];
+    if (lane == 0) s_m[warp] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0;
         T m2 = T(0);
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += s_tr[w]; m2 = fmax(m2, s_mx[w]); }
-        const double tau = 1.0 / mu[b];
-        svt_on[b] = a > tau * tau ? 1 : 0;
+        for (int w = 0; w < nw; ++w) m2 = fmax(m2, s_m[w]);
         scale[b] = m2;
     }
 }
 
-// h_j = max(1 - tau/sqrt(lambda_j), 0) from the Gram eigenvalues lambda_j =
-// diag(G) after Jacobi; J = A W diag(h) W^T (tall) or W diag(h) W^T A (wide)
-// equals U max(Sigma - tau, 0) V^T.  Also counts the SVT rank.
+// After the one-sided Jacobi the columns x_j of X are orthogonal and
+// ||x_j||^2 are the eigenvalues lambda_j of the Gram; the singular values of A
+// are sqrt(lambda_j).  h_j = max(1 - tau/||x_j||, 0), so that
+// J = X diag(h) W^T (tall) or W diag(h) X^T (wide) = U max(Sigma - tau, 0) V^T.
+// Also counts the SVT rank.  One CTA per block.
 template <typename T>
-__global__ void svt_weights(T* const* __restrict__ G, T* const* __restrict__ h, const int* __restrict__ p,
-                            const int* __restrict__ pp, const int* __restrict__ act, const int* __restrict__ svt_on,
+__global__ void svt_weights(const OsjDesc<T>* __restrict__ descs, T* const* __restrict__ h,
+                            const int* __restrict__ act, const int* __restrict__ svt_on,
                             const double* __restrict__ mu, int* __restrict__ rank, int nblk) {
     const int b = blockIdx.x;
     if (b >= nblk || !act[b]) return;
-    const T* g = G[b];
+    const OsjDesc<T> d = descs[b];
     T* hb = h[b];
-    const int n = p[b], ld = pp[b];
     const double tau = 1.0 / mu[b];
     const T tau_t = (T)tau;
-    const T tau2 = (T)(tau * tau);
     const int on = svt_on[b];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int cnt = 0;
-    for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+    for (int j = warp; j < d.pp; j += nw) {
         T w = T(0);
-        if (on && i < n) {
-            const T lam = g[i + (int64_t)i * ld];
-            if (lam > tau2) {
-                w = T(1) - tau_t / sqrt(lam);
-                if (w > T(0)) ++cnt; else w = T(0);
-            }
+        if (on && j < d.p) {
+            const T* x = d.X + (int64_t)j * d.ldx;
+            T acc = T(0);
+            for (int i = lane; i < d.L; i += 32) acc += x[i] * x[i];
+            const T nrm = sqrt(warp_sum(acc));
+            if (nrm > tau_t) w = T(1) - tau_t / nrm;
         }
-        hb[i] = w;
+        if (lane == 0) {
+            hb[j] = w;
+            if (w > T(0)) ++cnt;
+        }
     }
     __shared__ int s_c[32];
-    cnt = __reduce_add_sync(0xffffffffu, cnt);
-    if ((threadIdx.x & 31) == 0) s_c[threadIdx.x >> 5] = cnt;
+    if (lane == 0) s_c[warp] = cnt;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int a = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += s_c[w];
-        rank[b] = a;
+        int a2 = 0;
+        for (int w2 = 0; w2 < nw; ++w2) a2 += s_c[w2];
+        rank[b] = a2;
     }
 }
 
@@ -153,7 +160,7 @@ __global__ void z_update(int r, int64_t n, const int* __restrict__ colblk, const
                          const double* __restrict__ mu, double rho, double mu_max, const T* __restrict__ Tt,
                          const T* __restrict__ Jt, T* __restrict__ Y2t, T* __restrict__ Zt, T* __restrict__ D,
                          T* __restrict__ A, const T* __restrict__ sig, const T* __restrict__ dinv,
-                         T* __restrict__ dmax) {
+                         T* __restrict__ dmax, double* __restrict__ afro) {
     const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= n) return;
@@ -163,20 +170,26 @@ __global__ void z_update(int r, int64_t n, const int* __restrict__ colblk, const
     const double mun = fmin(rho * mud, mu_max);
     const T imu = (T)(1.0 / mud), muT = (T)mud, imun = (T)(1.0 / mun);
     const int64_t o = j * r;
-    T acc = T(0);
+    T acc = T(0), aacc = T(0);
     for (int i = lane; i < r; i += 32) {
         const T tv = Tt[o + i], jv = Jt[o + i], y2 = Y2t[o + i];
         const T z = dinv[i] * (sig[i] * tv + jv - y2 * imu);
         const T dd = z - jv;
         const T y2n = y2 + muT * dd;
+        const T av = z + y2n * imun;
         Zt[o + i] = z;
         D[o + i] = dd;
         Y2t[o + i] = y2n;
-        A[o + i] = z + y2n * imun;
+        A[o + i] = av;
         acc += dd * dd;
+        aacc += av * av;
     }
     acc = warp_sum(acc);
-    if (lane == 0) atomic_max_nonneg(&dmax[b], sqrt(acc));
+    aacc = warp_sum(aacc);
+    if (lane == 0) {
+        atomic_max_nonneg(&dmax[b], sqrt(acc));
+        atomicAdd(&afro[b], (double)aacc);   // ||A||_F^2 of the next SVT input
+    }
 }
 
 // E-step (column shrinkage), primal residual, Y1 dual step and the next
@@ -223,13 +236,16 @@ __global__ void e_update(int64_t m, int64_t n, const int* __restrict__ colblk, c
 // max |V D| <= nu * max_j ||D_j|| (nu = largest row norm of V) decides
 // convergence when that bound is already below eps; otherwise the exact value
 // is needed (a product with V).
+// ||V d||_inf >= ||V d||_2 / sqrt(n) = ||d||_2 / sqrt(n) (V has orthonormal
+// columns), so max_j ||D_j|| / sqrt(n) >= eps already rules convergence out.
 template <typename T>
 __global__ void stop_part1(int nblk, const int* __restrict__ act, const T* __restrict__ r1, const T* __restrict__ dmax,
-                           T nu, double eps, int* __restrict__ need_exact, int* __restrict__ conv_bound) {
+                           T nu, double inv_sqrt_n, double eps, int* __restrict__ need_exact,
+                           int* __restrict__ conv_bound) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nblk) return;
     int ne = 0, cb = 0;
-    if (act[b] && (double)r1[b] < eps) {
+    if (act[b] && (double)r1[b] < eps && (double)dmax[b] * inv_sqrt_n < eps) {
         if ((double)(nu * dmax[b]) < eps) cb = 1; else ne = 1;
     }
     need_exact[b] = ne;
@@ -242,7 +258,7 @@ __global__ void stop_part2(int nblk, int* __restrict__ act, int* __restrict__ it
                            T* __restrict__ dmax, T* __restrict__ r2x, const int* __restrict__ need_exact,
                            const int* __restrict__ conv_bound, T nu, double* __restrict__ resid,
                            const int* __restrict__ rank_cur, int* __restrict__ rank_fin, int* __restrict__ conv,
-                           double* __restrict__ mu_fin) {
+                           double* __restrict__ mu_fin, double* __restrict__ afro) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nblk) return;
     if (act[b]) {
@@ -367,6 +383,31 @@ __global__ void gather_normalise_f64(const T* __restrict__ src, int64_t ld, int6
 __global__ void ns_combine(double* __restrict__ X, const double* __restrict__ Y, int64_t count) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
         X[i] = 1.5 * X[i] - 0.5 * Y[i];
+}
+
+// Given Y = W (W^T W): Wi <- 2 W - Y (= W (2I - W^T W), the first-order
+// inverse transpose W^{-T}) and W <- 1.5 W - 0.5 Y (one Newton-Schulz step
+// towards orthogonality).  Rotations accumulated in float32 drift from
+// orthogonal by ~eps per round; with Wi in the SVT reconstruction the drift
+// enters J only at second order, and the Newton-Schulz step keeps the warm
+// start of the next iteration orthogonal.
+template <typename T>
+__global__ void ns_orth(T* const* __restrict__ W, T* const* __restrict__ Y, T* const* __restrict__ Wi,
+                        const int* __restrict__ p, const int* __restrict__ pp, const int* __restrict__ on, int nblk) {
+    const int b = blockIdx.y;
+    if (b >= nblk || !on[b]) return;
+    const int n = p[b], ld = pp[b];
+    T* w = W[b];
+    T* wi = Wi[b];
+    const T* y = Y[b];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        const int64_t o = i + (int64_t)j * ld;
+        const T wv = w[o], yv = y[o];
+        wi[o] = T(2) * wv - yv;
+        w[o] = T(1.5) * wv - T(0.5) * yv;
+    }
 }
 
 }  // namespace k

@@ -8,6 +8,7 @@
 // and a second kernel applies the accumulated rotations R_P to the
 // off-diagonal tiles (G <- R^T G R) and to the eigenvector matrix (W <- W R).
 #include "common.cuh"
+#include "inner_jacobi.cuh"
 #include "kernels.cuh"
 
 namespace lrr {
@@ -15,10 +16,6 @@ namespace {
 
 constexpr int NT = 256;
 
-// item at position `pos` of round `r` in the circle-method schedule of N items
-__device__ __forceinline__ int circle_item(int pos, int r, int N) {
-    return pos == 0 ? 0 : 1 + ((pos - 1 + r) % (N - 1));
-}
 
 // global row of local index i (0..2b-1) of the pivot pair (a, c)
 __device__ __forceinline__ int pair_row(int i, int a, int c, int b) { return i < b ? a * b + i : c * b + (i - b); }
@@ -40,7 +37,13 @@ __global__ void __launch_bounds__(NT) jac_solve(const JacDesc<T>* __restrict__ d
     __shared__ int pi[b], qi[b];
     __shared__ T red[NT / 32];
     const int t = threadIdx.x;
-    const T floor_abs = num<T>::eps() * (*d.scale) + num<T>::tiny();
+    // Off-diagonal entries below the rounding noise of the Gram products
+    // (~sqrt(order) * eps * max|G_ii|) carry no information and do not count
+    // towards the convergence measure; they are still rotated away like any
+    // other entry above eps * sqrt(G_ii G_jj), so a converged sweep leaves the
+    // resolved part of the spectrum at working accuracy.
+    const T floor_abs = T(4) * sqrt(T(d.pp)) * num<T>::eps() * (*d.scale) + num<T>::tiny();
+    const T floor_rot = num<T>::eps() * num<T>::eps() * (*d.scale) + num<T>::tiny();
 
     for (int e = t; e < B2 * B2; e += NT) {
         const int i = e % B2, j = e / B2;
@@ -49,13 +52,17 @@ __global__ void __launch_bounds__(NT) jac_solve(const JacDesc<T>* __restrict__ d
     }
     __syncthreads();
 
-    // convergence measure of this pivot block before rotating it
+    // convergence measure of this pivot block before rotating it, and whether
+    // any entry is large enough to rotate at all
     T offm = T(0);
+    int any = 0;
     for (int e = t; e < B2 * B2; e += NT) {
         const int i = e % B2, j = e / B2;
         if (i < j) {
             const T v = fabs(S[i][j]);
-            if (v > floor_abs) offm = fmax(offm, v / sqrt(fabs(S[i][i] * S[j][j]) + num<T>::tiny()));
+            const T sc = sqrt(fabs(S[i][i] * S[j][j]));
+            if (v > floor_abs) offm = fmax(offm, v / (sc + num<T>::tiny()));
+            if (v > floor_rot && v > num<T>::eps() * sc) any = 1;
         }
     }
     offm = warp_max(offm);
@@ -65,67 +72,19 @@ __global__ void __launch_bounds__(NT) jac_solve(const JacDesc<T>* __restrict__ d
         T mx = T(0);
         for (int w = 0; w < NT / 32; ++w) mx = fmax(mx, red[w]);
         atomic_max_nonneg(d.off, mx);
-        red[0] = mx;
     }
-    __syncthreads();
-    const bool need = red[0] > tol;
+    const bool need = __syncthreads_or(any) != 0;
 
-    if (need) {
-        for (int sweep = 0; sweep < 6; ++sweep) {
-            int rotated = 0;
-            for (int r = 0; r < B2 - 1; ++r) {
-                if (t < b) {
-                    const int p = circle_item(t, r, B2), q = circle_item(B2 - 1 - t, r, B2);
-                    const T app = S[p][p], aqq = S[q][q], apq = S[p][q];
-                    T cc = T(1), ss = T(0);
-                    if (fabs(apq) > floor_abs && fabs(apq) > num<T>::eps() * sqrt(fabs(app * aqq))) {
-                        const T theta = (aqq - app) / (T(2) * apq);
-                        T tt;
-                        if (fabs(theta) > T(1) / num<T>::eps()) tt = T(0.5) / theta;
-                        else tt = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
-                        cc = T(1) / sqrt(tt * tt + T(1));
-                        ss = tt * cc;
-                        rotated = 1;
-                    }
-                    cs[t] = cc; sn[t] = ss; pi[t] = p; qi[t] = q;
-                }
-                __syncthreads();
-                // S <- J^T S J on all 2x2 sub-blocks at once; R <- R J
-                for (int e = t; e < b * b; e += NT) {
-                    const int k = e % b, l = e / b;
-                    const int p = pi[k], q = qi[k], u = pi[l], v = qi[l];
-                    const T ck = cs[k], sk = sn[k], cl = cs[l], sl = sn[l];
-                    const T s_pu = S[p][u], s_pv = S[p][v], s_qu = S[q][u], s_qv = S[q][v];
-                    // rows: (J^T S)
-                    const T r_pu = ck * s_pu - sk * s_qu, r_pv = ck * s_pv - sk * s_qv;
-                    const T r_qu = sk * s_pu + ck * s_qu, r_qv = sk * s_pv + ck * s_qv;
-                    // columns: (.. J)
-                    S[p][u] = cl * r_pu - sl * r_pv;
-                    S[p][v] = sl * r_pu + cl * r_pv;
-                    S[q][u] = cl * r_qu - sl * r_qv;
-                    S[q][v] = sl * r_qu + cl * r_qv;
-                }
-                for (int e = t; e < B2 * b; e += NT) {
-                    const int i = e % B2, l = e / B2;
-                    const int u = pi[l], v = qi[l];
-                    const T cl = cs[l], sl = sn[l];
-                    const T x = R[i][u], y = R[i][v];
-                    R[i][u] = cl * x - sl * y;
-                    R[i][v] = sl * x + cl * y;
-                }
-                __syncthreads();
-                if (t < b && sn[t] != T(0)) { S[pi[t]][qi[t]] = T(0); S[qi[t]][pi[t]] = T(0); }
-                __syncthreads();
-            }
-            if (!__syncthreads_or(rotated)) break;
-        }
-    }
+    const int any_rot = need ? inner_jacobi<T, B2, NT>(S, R, cs, sn, pi, qi, floor_rot, floor_abs, 6) : 0;
     // diagonalised pivot block back into G, rotation out for the apply kernel
-    T* Rg = d.R + (int64_t)P * B2 * B2;
-    for (int e = t; e < B2 * B2; e += NT) {
-        const int i = e % B2, j = e / B2;
-        if (need) d.G[pair_row(i, a, c, b) + (int64_t)pair_row(j, a, c, b) * d.pp] = S[i][j];
-        Rg[e] = R[i][j];
+    if (t == 0) d.rot[P] = any_rot;
+    if (any_rot) {
+        T* Rg = d.R + (int64_t)P * B2 * B2;
+        for (int e = t; e < B2 * B2; e += NT) {
+            const int i = e % B2, j = e / B2;
+            d.G[pair_row(i, a, c, b) + (int64_t)pair_row(j, a, c, b) * d.pp] = S[i][j];
+            Rg[e] = R[i][j];
+        }
     }
 }
 
@@ -151,6 +110,8 @@ __global__ void __launch_bounds__(NT) jac_apply(const JacDesc<T>* __restrict__ d
         int P = 0, rem = tile;
         while (rem >= npairs - 1 - P) { rem -= npairs - 1 - P; ++P; }
         const int Qp = P + 1 + rem;
+        const int rP = d.rot[P], rQ = d.rot[Qp];
+        if (!rP && !rQ) return;
         const int a = circle_item(P, round, nb), c = circle_item(nb - 1 - P, round, nb);
         const int a2 = circle_item(Qp, round, nb), c2 = circle_item(nb - 1 - Qp, round, nb);
         const T* RP = d.R + (int64_t)P * B2 * B2;
@@ -158,7 +119,7 @@ __global__ void __launch_bounds__(NT) jac_apply(const JacDesc<T>* __restrict__ d
         for (int e = t; e < B2 * B2; e += NT) {
             const int i = e % B2, j = e / B2;
             X[i][j] = d.G[pair_row(i, a, c, b) + (int64_t)pair_row(j, a2, c2, b) * d.pp];
-            Q[i][j] = RQ[e];
+            Q[i][j] = rQ ? RQ[e] : (i == j ? T(1) : T(0));
         }
         __syncthreads();
         T acc[PER];
@@ -175,7 +136,7 @@ __global__ void __launch_bounds__(NT) jac_apply(const JacDesc<T>* __restrict__ d
         for (int u = 0; u < PER; ++u) {
             const int e = t + u * NT, i = e % B2, j = e / B2;
             X[i][j] = acc[u];
-            Q[i][j] = RP[e];
+            Q[i][j] = rP ? RP[e] : (i == j ? T(1) : T(0));
         }
         __syncthreads();
 #pragma unroll
@@ -192,6 +153,7 @@ __global__ void __launch_bounds__(NT) jac_apply(const JacDesc<T>* __restrict__ d
         // eigenvector tile: rows chunk ch, columns I_P:  W[ch, I_P] <- W[ch, I_P] R_P
         tile -= ntile_g;
         const int P = tile % npairs, ch = tile / npairs;
+        if (!d.rot[P]) return;
         const int a = circle_item(P, round, nb), c = circle_item(nb - 1 - P, round, nb);
         const T* RP = d.R + (int64_t)P * B2 * B2;
         for (int e = t; e < B2 * B2; e += NT) {

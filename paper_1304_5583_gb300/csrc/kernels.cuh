@@ -37,6 +37,7 @@ struct JacDesc {
     T* G;
     T* W;
     T* R;          // rotation scratch: (pp/(2bs)) * (2bs)^2 values
+    int* rot;      // per pivot pair of the current round: 1 if its rotation is not the identity
     int* done;     // per matrix: 1 when converged (checked before each sweep)
     T* off;        // per matrix: max scaled off-diagonal seen in the current sweep
     const int* active;  // optional: skip when *active == 0
@@ -50,6 +51,24 @@ struct JacDesc {
 // double, 32 for float.  `done` and `off` are reset at entry.
 template <typename T>
 cudaError_t jacobi_sweeps(const JacDesc<T>* d_desc, int nmat, int max_pp, int sweeps, T tol, cudaStream_t s);
+// One-sided block Jacobi (osj.cu): X (L x p, ld ldx) is rotated to orthogonal
+// columns together with W (p x p, ld ldw); pp = p rounded up to 2*bs.
+template <typename T>
+struct OsjDesc {
+    T* X;
+    T* W;
+    int* done;
+    T* off;
+    const int* active;
+    const T* scale;     // largest squared column norm of X
+    int64_t ldx, ldw;
+    int L, p, pp;
+};
+
+template <typename T>
+cudaError_t osj_sweeps(const OsjDesc<T>* d_desc, int nmat, int max_pp, int sweeps, T tol, int* sweeps_run,
+                       cudaStream_t s);
+
 template <typename T> constexpr int jacobi_bs() { return sizeof(T) == 8 ? 16 : 32; }
 
 }  // namespace lrr

@@ -1,0 +1,263 @@
+// Batched one-sided block-Jacobi SVD for the singular-value thresholding step.
+//
+// For every block the L x p matrix X (X = A W for a tall A, X = A^T W for a
+// wide one, W the previous iteration's right basis) is driven to orthogonal
+// columns by rotations X <- X R, W <- W R.  In each round the p/b column
+// blocks are paired round-robin and one CTA per pair
+//   1. forms the 2b x 2b Gram S = X_P^T X_P afresh from the columns of X
+//      (so each entry carries only the rounding of its own two columns),
+//   2. diagonalises S in shared memory (inner cyclic Jacobi),
+//   3. applies the accumulated rotation to X_P and W_P in row chunks.
+// Pairs of a round touch disjoint columns, so one launch per round suffices.
+// A matrix is converged once a whole sweep saw every pivot Gram with
+// max |s_ij| / sqrt(s_ii s_jj) <= tol; then the squared column norms of X are
+// the eigenvalues of the Gram A^T A (or A A^T) and W holds its eigenvectors.
+#include "common.cuh"
+#include "inner_jacobi.cuh"
+#include "kernels.cuh"
+
+namespace lrr {
+namespace {
+
+constexpr int NT = 256;
+
+__device__ __forceinline__ int pcol(int i, int a, int c, int b) { return i < b ? a * b + i : c * b + (i - b); }
+
+template <typename T, int B2>
+__global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ descs, int round) {
+    constexpr int b = B2 / 2;
+    constexpr int TI = B2 / 16;        // each thread owns a TI x TI tile of the B2 x B2 products
+    constexpr int LD = B2 + 4;         // padded row stride of the shared tiles
+    const OsjDesc<T> d = descs[blockIdx.y];
+    if (d.active && *d.active == 0) return;
+    if (*d.done) return;
+    const int nb = d.pp / b, npairs = nb / 2;
+    const int P = blockIdx.x;
+    if (P >= npairs) return;
+    const int a = circle_item(P, round, nb), c = circle_item(nb - 1 - P, round, nb);
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* Xs = reinterpret_cast<T*>(smem_raw);          // B2 rows x LD
+    T(*S)[B2 + 1] = reinterpret_cast<T(*)[B2 + 1]>(Xs + B2 * LD);
+    T(*R)[B2 + 1] = S + B2;
+    __shared__ T cs[b], sn[b];
+    __shared__ int pi[b], qi[b];
+    __shared__ T red[NT / 32];
+    const int t = threadIdx.x;
+    const int ti = t % 16, tj = t / 16;     // tile coordinates: rows ti*TI.., cols tj*TI..
+    // columns whose norm is below ~64 eps times the largest column are rounding
+    // noise of earlier rotations: their mutual angles carry no information
+    const T noise = T(64) * num<T>::eps();
+    const T floor2 = noise * noise * (*d.scale) + num<T>::tiny();
+
+    // 1. pivot Gram S = X_P^T X_P from the columns of X.  Partial sums over
+    //    B2-row chunks are formed in T and added into float64 accumulators:
+    //    a float32 sum over all L rows would leave noise ~sqrt(L) eps in every
+    //    scaled entry, which caps how orthogonal the columns can be made; with
+    //    chunked float64 accumulation it drops to ~sqrt(B2) eps / sqrt(L/B2).
+    double acc[TI][TI];
+#pragma unroll
+    for (int u = 0; u < TI; ++u)
+#pragma unroll
+        for (int v = 0; v < TI; ++v) acc[u][v] = 0.0;
+    for (int r0 = 0; r0 < d.L; r0 += B2) {
+        for (int e = t; e < B2 * B2; e += NT) {
+            const int rr = e % B2, cc = e / B2;
+            const int gr = r0 + rr, gc = pcol(cc, a, c, b);
+            Xs[rr * LD + cc] = (gr < d.L && gc < d.p) ? d.X[gr + (int64_t)gc * d.ldx] : T(0);
+        }
+        __syncthreads();
+        T part[TI][TI];
+#pragma unroll
+        for (int u = 0; u < TI; ++u)
+#pragma unroll
+            for (int v = 0; v < TI; ++v) part[u][v] = T(0);
+#pragma unroll 4
+        for (int rr = 0; rr < B2; ++rr) {
+            T xi[TI], xj[TI];
+#pragma unroll
+            for (int u = 0; u < TI; ++u) { xi[u] = Xs[rr * LD + ti * TI + u]; xj[u] = Xs[rr * LD + tj * TI + u]; }
+#pragma unroll
+            for (int u = 0; u < TI; ++u)
+#pragma unroll
+                for (int v = 0; v < TI; ++v) part[u][v] = fma(xi[u], xj[v], part[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < TI; ++u)
+#pragma unroll
+            for (int v = 0; v < TI; ++v) acc[u][v] += (double)part[u][v];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < TI; ++u)
+#pragma unroll
+        for (int v = 0; v < TI; ++v) {
+            const int i = ti * TI + u, j = tj * TI + v;
+            S[i][j] = (T)acc[u][v];
+            R[i][j] = (i == j) ? T(1) : T(0);
+        }
+    __syncthreads();
+
+    // 2. convergence measure before rotating (noise columns excluded)
+    T offm = T(0);
+    for (int e = t; e < B2 * B2; e += NT) {
+        const int i = e % B2, j = e / B2;
+        if (i < j && S[i][i] > floor2 && S[j][j] > floor2)
+            offm = fmax(offm, fabs(S[i][j]) / sqrt(S[i][i] * S[j][j]));
+    }
+    offm = warp_max(offm);
+    if ((t & 31) == 0) red[t >> 5] = offm;
+    __syncthreads();
+    if (t == 0) {
+        T mx = T(0);
+        for (int w = 0; w < NT / 32; ++w) mx = fmax(mx, red[w]);
+        atomic_max_nonneg(d.off, mx);
+    }
+
+    // 3. rotate the pivot Gram to diagonal form; rotations that only mix noise
+    //    columns (|s_pq| below floor2) do not keep the inner sweeps going
+    const int rot = inner_jacobi<T, B2, NT>(S, R, cs, sn, pi, qi, num<T>::tiny(), floor2, 4);
+    if (!rot) return;
+
+    // R is a product of some thousand plane rotations, orthogonal only to
+    // ~sqrt(count) eps.  Applied to graded columns that defect would mix
+    // eps-sized parts of the large columns into the small ones and cap the
+    // attainable orthogonality, so one Newton-Schulz step R <- R (3I - R^T R)/2
+    // restores orthogonality to ~eps^2 before R touches X and W.
+    {
+        T g[TI][TI];
+#pragma unroll
+        for (int u = 0; u < TI; ++u)
+#pragma unroll
+            for (int v = 0; v < TI; ++v) g[u][v] = T(0);
+        for (int k = 0; k < B2; ++k) {
+            T ri[TI], rj[TI];
+#pragma unroll
+            for (int u = 0; u < TI; ++u) { ri[u] = R[k][ti * TI + u]; rj[u] = R[k][tj * TI + u]; }
+#pragma unroll
+            for (int u = 0; u < TI; ++u)
+#pragma unroll
+                for (int v = 0; v < TI; ++v) g[u][v] = fma(ri[u], rj[v], g[u][v]);
+        }
+        // Xs (free here) holds R^T R
+#pragma unroll
+        for (int u = 0; u < TI; ++u)
+#pragma unroll
+            for (int v = 0; v < TI; ++v) Xs[(ti * TI + u) * LD + tj * TI + v] = g[u][v];
+        __syncthreads();
+        T y[TI][TI];
+#pragma unroll
+        for (int u = 0; u < TI; ++u)
+#pragma unroll
+            for (int v = 0; v < TI; ++v) y[u][v] = T(0);
+        for (int k = 0; k < B2; ++k) {
+            T ri[TI], gk[TI];
+#pragma unroll
+            for (int u = 0; u < TI; ++u) { ri[u] = R[ti + 16 * u][k]; gk[u] = Xs[k * LD + tj * TI + u]; }
+#pragma unroll
+            for (int u = 0; u < TI; ++u)
+#pragma unroll
+                for (int v = 0; v < TI; ++v) y[u][v] = fma(ri[u], gk[v], y[u][v]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < TI; ++u)
+#pragma unroll
+            for (int v = 0; v < TI; ++v) {
+                const int i = ti + 16 * u, j = tj * TI + v;
+                R[i][j] = T(1.5) * R[i][j] - T(0.5) * y[u][v];
+            }
+        __syncthreads();
+    }
+
+    // 4. X_P <- X_P R and W_P <- W_P R, row chunk by row chunk
+    for (int pass = 0; pass < 2; ++pass) {
+        T* base = pass == 0 ? d.X : d.W;
+        const int64_t ld = pass == 0 ? d.ldx : d.ldw;
+        const int rows = pass == 0 ? d.L : d.p;
+        for (int r0 = 0; r0 < rows; r0 += B2) {
+            for (int e = t; e < B2 * B2; e += NT) {
+                const int rr = e % B2, cc = e / B2;
+                const int gr = r0 + rr, gc = pcol(cc, a, c, b);
+                Xs[rr * LD + cc] = (gr < rows && gc < d.p) ? base[gr + (int64_t)gc * ld] : T(0);
+            }
+            __syncthreads();
+            T out[TI][TI];
+#pragma unroll
+            for (int u = 0; u < TI; ++u)
+#pragma unroll
+                for (int v = 0; v < TI; ++v) out[u][v] = T(0);
+#pragma unroll 4
+            for (int k = 0; k < B2; ++k) {
+                T xr[TI], rk[TI];
+#pragma unroll
+                for (int u = 0; u < TI; ++u) { xr[u] = Xs[(ti + 16 * u) * LD + k]; rk[u] = R[k][tj * TI + u]; }
+#pragma unroll
+                for (int u = 0; u < TI; ++u)
+#pragma unroll
+                    for (int v = 0; v < TI; ++v) out[u][v] = fma(xr[u], rk[v], out[u][v]);
+            }
+#pragma unroll
+            for (int u = 0; u < TI; ++u)
+#pragma unroll
+                for (int v = 0; v < TI; ++v) {
+                    const int gr = r0 + ti + 16 * u, gc = pcol(tj * TI + v, a, c, b);
+                    if (gr < rows && gc < d.p) base[gr + (int64_t)gc * ld] = out[u][v];
+                }
+            __syncthreads();
+        }
+    }
+}
+
+template <typename T>
+__global__ void osj_reset(const OsjDesc<T>* __restrict__ descs, int nmat) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nmat) return;
+    *descs[i].done = 0;
+    *descs[i].off = T(0);
+}
+
+template <typename T>
+__global__ void osj_check(const OsjDesc<T>* __restrict__ descs, int nmat, T tol, int* __restrict__ sweeps_run) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nmat) return;
+    const OsjDesc<T> d = descs[i];
+    if (d.active && *d.active == 0) return;
+    if (*d.done == 0) {
+        if (sweeps_run) sweeps_run[i] += 1;
+        // the pivot Grams are accumulated in float64 over float32 chunk sums, so
+        // their noise is a few eps relative to sqrt(s_ii s_jj)
+        const T t_eff = fmax(tol, T(64) * num<T>::eps());
+        if (*d.off <= t_eff) *d.done = 1;
+    }
+    *d.off = T(0);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t osj_sweeps(const OsjDesc<T>* d_desc, int nmat, int max_pp, int sweeps, T tol, int* sweeps_run,
+                       cudaStream_t s) {
+    constexpr int b = jacobi_bs<T>();
+    constexpr int B2 = 2 * b;
+    if (nmat <= 0 || max_pp <= 0) return cudaSuccess;
+    const int nb = max_pp / b, npairs = nb / 2;
+    const size_t smem = sizeof(T) * (B2 * (B2 + 4) + 2 * B2 * (B2 + 1));
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(osj_round<T, B2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
+    osj_reset<T><<<ceil_div(nmat, 128), 128, 0, s>>>(d_desc, nmat);
+    const dim3 g((unsigned)npairs, (unsigned)nmat);
+    for (int sw = 0; sw < sweeps; ++sw) {
+        for (int r = 0; r < nb - 1; ++r) osj_round<T, B2><<<g, NT, smem, s>>>(d_desc, r);
+        osj_check<T><<<ceil_div(nmat, 128), 128, 0, s>>>(d_desc, nmat, tol, sweeps_run);
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t osj_sweeps<float>(const OsjDesc<float>*, int, int, int, float, int*, cudaStream_t);
+template cudaError_t osj_sweeps<double>(const OsjDesc<double>*, int, int, int, double, int*, cudaStream_t);
+
+}  // namespace lrr

@@ -88,15 +88,22 @@ struct Buffers {
     T *Zt, *Jt, *Y2t, *A, *D, *Tt;
     // per block
     std::vector<T*> G, W, H, R, h, T1;
+    std::vector<int*> rot;
+    int* rot_d;
     double *mu, *mu_fin, *resid;
     int *act, *iters, *svt_on, *rank_cur, *rank_fin, *need_exact, *conv_bound, *conv, *jdone, *colblk, *flag;
     T *r1, *dmax, *r2x, *jscale, *joff;
     int64_t* perm;
     // descriptor / pointer tables
     GemmDesc<T>* gd;       // 12 * t descriptors
-    JacDesc<T>* jd;
+    OsjDesc<T>* jd;
+    double* afro;
+    int* jsweeps;
     T** Gp;
     T** hp;
+    T** Wp;
+    T** Hp;
+    T** T1p;
     int *pv, *ppv;
     // C step
     int *kept, *kept_n;
@@ -147,15 +154,16 @@ Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector
     b.D = a.take<T>(r * n);
     b.Tt = a.take<T>(r * n);
     const int t = p->t;
-    b.G.resize(t); b.W.resize(t); b.H.resize(t); b.R.resize(t); b.h.resize(t); b.T1.resize(t);
+    b.G.resize(t); b.W.resize(t); b.H.resize(t); b.R.resize(t); b.h.resize(t); b.T1.resize(t); b.rot.resize(t);
+    b.rot_d = a.take<int>(mpp / B2d);
     for (int i = 0; i < t; ++i) {
         const int64_t pp = blk[i].ppmax;
-        b.G[i] = a.take<T>(pp * pp);
         b.W[i] = a.take<T>(pp * pp);
         b.H[i] = a.take<T>(pp * pp);
         b.T1[i] = a.take<T>(pp * pp);
         b.R[i] = a.take<T>(pp * B2);
         b.h[i] = a.take<T>(pp);
+        b.rot[i] = a.take<int>(pp / B2);
     }
     b.mu = a.take<double>(t);
     b.mu_fin = a.take<double>(t);
@@ -178,9 +186,14 @@ Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector
     b.joff = a.take<T>(t);
     b.perm = a.take<int64_t>(n);
     b.gd = a.take<GemmDesc<T>>(16 * (size_t)t + 16);
-    b.jd = a.take<JacDesc<T>>(t);
+    b.jd = a.take<OsjDesc<T>>(t);
+    b.afro = a.take<double>(t);
+    b.jsweeps = a.take<int>(t);
     b.Gp = a.take<T*>(t);
     b.hp = a.take<T*>(t);
+    b.Wp = a.take<T*>(t);
+    b.Hp = a.take<T*>(t);
+    b.T1p = a.take<T*>(t);
     b.pv = a.take<int>(t);
     b.ppv = a.take<int>(t);
     const int64_t p0 = blk[0].ppmax;
@@ -211,6 +224,52 @@ std::vector<BlockInfo<T>> block_info(const lrr_problem* p) {
 inline unsigned grid1(int64_t count, int threads = 256) {
     return (unsigned)std::min<int64_t>((count + threads - 1) / threads, 152 * 32);
 }
+
+// Per-phase CUDA-event timing on the solve's stream plus launch counting.
+struct Prof {
+    bool on = false;
+    cudaStream_t s = nullptr;
+    double ms[LRR_NPHASE] = {};
+    int64_t calls[LRR_NPHASE] = {};
+    int64_t launches = 0, iterations = 0;
+    std::vector<cudaEvent_t> free_ev;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    cudaEvent_t open_ev = nullptr;
+    cudaEvent_t get() {
+        if (!free_ev.empty()) { cudaEvent_t e = free_ev.back(); free_ev.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void begin() {
+        if (!on) return;
+        open_ev = get();
+        cudaEventRecord(open_ev, s);
+    }
+    void end(int ph, int64_t nlaunch) {
+        launches += nlaunch;
+        calls[ph] += nlaunch;
+        if (!on || !open_ev) return;
+        cudaEvent_t e = get();
+        cudaEventRecord(e, s);
+        pending.push_back({ph, {open_ev, e}});
+        open_ev = nullptr;
+    }
+    // after a stream synchronisation: fold the recorded pairs into ms[]
+    void flush() {
+        for (auto& p : pending) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, p.second.first, p.second.second) == cudaSuccess) ms[p.first] += t;
+            free_ev.push_back(p.second.first);
+            free_ev.push_back(p.second.second);
+        }
+        pending.clear();
+    }
+    ~Prof() {
+        for (auto& p : pending) { cudaEventDestroy(p.second.first); cudaEventDestroy(p.second.second); }
+        for (auto e : free_ev) cudaEventDestroy(e);
+    }
+};
 
 template <typename T>
 GemmDesc<T> gdesc(const T* A, int64_t lda, const T* B, int64_t ldb, T* C, int64_t ldc, int m, int n, int k,
@@ -253,6 +312,9 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     const int t = p->t;
     const Tin* M = static_cast<const Tin*>(p->M);
 
+    Prof prof;
+    prof.on = o->profile != 0;
+    prof.s = s;
     cudaEvent_t ev[4];
     for (auto& e : ev) LRR_CUDA_TRY(cudaEventCreate(&e));
     struct EvFree {
@@ -303,7 +365,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         for (double v : dg) sc = std::max(sc, std::fabs(v));
         if (!(sc > 0)) return LRR_ERR_RANK;
         JacDesc<double> jd{};
-        jd.G = B.Kd; jd.W = B.Wd; jd.R = B.Rd; jd.done = B.jac_done_d; jd.off = B.jac_off_d;
+        jd.G = B.Kd; jd.W = B.Wd; jd.R = B.Rd; jd.rot = B.rot_d; jd.done = B.jac_done_d; jd.off = B.jac_off_d;
         jd.active = nullptr; jd.scale = B.jac_scale_d; jd.pp = B.mpp;
         LRR_CUDA_TRY(cudaMemcpyAsync(B.jac_scale_d, &sc, sizeof(double), cudaMemcpyHostToDevice, s));
         LRR_CUDA_TRY(cudaMemcpyAsync(B.jac_setup, &jd, sizeof(jd), cudaMemcpyHostToDevice, s));
@@ -337,6 +399,12 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     LRR_CUDA_TRY(cudaMemcpyAsync(&nu_h, B.nu, sizeof(T), cudaMemcpyDeviceToHost, s));
     LRR_CUDA_TRY(cudaStreamSynchronize(s));
     LRR_CUDA_TRY(cudaEventRecord(ev[1], s));
+    {
+        const int64_t nbd = B.mpp / jacobi_bs<double>();
+        const int64_t setup_launches = 1 + (need_md ? 1 : 0) + 2 + 1 + 2 + (1 + 40 * (2 * (nbd - 1) + 1)) + 2 + 1 + 1 + 1;
+        prof.launches += setup_launches;
+        prof.calls[LRR_PH_SETUP] += setup_launches;
+    }
 
     // ---- per-block tables (sizes now known: p_i = min(r, l_i))
     constexpr int B2 = 2 * jacobi_bs<T>();
@@ -351,17 +419,22 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         max_pp = std::max(max_pp, ppv[i]);
         max_l = std::max(max_l, blk[i].l);
     }
-    LRR_CUDA_TRY(cudaMemcpyAsync(B.Gp, B.G.data(), sizeof(T*) * t, cudaMemcpyHostToDevice, s));
     LRR_CUDA_TRY(cudaMemcpyAsync(B.hp, B.h.data(), sizeof(T*) * t, cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.Wp, B.W.data(), sizeof(T*) * t, cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.Hp, B.H.data(), sizeof(T*) * t, cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.T1p, B.T1.data(), sizeof(T*) * t, cudaMemcpyHostToDevice, s));
     LRR_CUDA_TRY(cudaMemcpyAsync(B.pv, pv.data(), sizeof(int) * t, cudaMemcpyHostToDevice, s));
     LRR_CUDA_TRY(cudaMemcpyAsync(B.ppv, ppv.data(), sizeof(int) * t, cudaMemcpyHostToDevice, s));
-    std::vector<JacDesc<T>> jdh((size_t)t);
+    std::vector<OsjDesc<T>> jdh((size_t)t);
     for (int i = 0; i < t; ++i) {
-        JacDesc<T>& j = jdh[i];
-        j.G = B.G[i]; j.W = B.W[i]; j.R = B.R[i]; j.done = B.jdone + i; j.off = B.joff + i;
-        j.active = B.svt_on + i; j.scale = B.jscale + i; j.pp = ppv[i];
+        OsjDesc<T>& j = jdh[i];
+        j.X = B.D + blk[i].col0 * r;
+        j.ldx = tall[i] ? r : blk[i].l;
+        j.L = tall[i] ? r : blk[i].l;
+        j.W = B.W[i]; j.ldw = ppv[i]; j.p = pv[i]; j.pp = ppv[i];
+        j.done = B.jdone + i; j.off = B.joff + i; j.active = B.svt_on + i; j.scale = B.jscale + i;
     }
-    LRR_CUDA_TRY(cudaMemcpyAsync(B.jd, jdh.data(), sizeof(JacDesc<T>) * t, cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.jd, jdh.data(), sizeof(OsjDesc<T>) * t, cudaMemcpyHostToDevice, s));
 
     // grouped GEMM descriptor sets
     std::vector<GemmDesc<T>> gh;
@@ -373,40 +446,44 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         sets.push_back(g);
         return (int)sets.size() - 1;
     };
-    std::vector<GemmDesc<T>> gram_tall, gram_wide, warm1, warm2, hmat, j_tall, j_wide, tmul, mzmul, exact;
+    std::vector<GemmDesc<T>> xw_tall, xw_wide, jmul, tmul, mzmul, exact, orth1, orth2;
     for (int i = 0; i < t; ++i) {
         const int64_t c0 = blk[i].col0;
         const int l = blk[i].l, pp_ = ppv[i], pi = pv[i];
         T* Ai = B.A + c0 * r;
+        // X = A W (tall) or A^T W (wide): A rotated into the previous right
+        // basis; the one-sided Jacobi then finishes orthogonalising its columns
+        T* Xi = B.D + c0 * r;
         if (tall[i]) {
-            gram_tall.push_back(gdesc<T>(Ai, r, Ai, r, B.G[i], pp_, l, l, r, B.act + i));
-            j_tall.push_back(gdesc<T>(Ai, r, B.H[i], pp_, B.Jt + c0 * r, r, r, l, l, B.act + i));
+            xw_tall.push_back(gdesc<T>(Ai, r, B.W[i], pp_, Xi, r, r, l, l, B.svt_on + i));
+            // J = X diag(h) W^{-1}:  A = X W^{-1}, so this keeps the kept directions only
+            GemmDesc<T> jd_ = gdesc<T>(Xi, r, B.T1[i], pp_, B.Jt + c0 * r, r, r, l, l, B.act + i);
+            jd_.kscale = B.h[i];
+            jmul.push_back(jd_);
         } else {
-            gram_wide.push_back(gdesc<T>(Ai, r, Ai, r, B.G[i], pp_, r, r, l, B.act + i));
-            j_wide.push_back(gdesc<T>(B.H[i], pp_, Ai, r, B.Jt + c0 * r, r, r, l, r, B.act + i));
+            xw_wide.push_back(gdesc<T>(Ai, r, B.W[i], pp_, Xi, l, l, r, r, B.svt_on + i));
+            // J = W^{-T} diag(h) X^T:  A^T = X W^{-1}
+            GemmDesc<T> jd_ = gdesc<T>(B.T1[i], pp_, Xi, l, B.Jt + c0 * r, r, r, l, r, B.act + i);
+            jd_.kscale = B.h[i];
+            jmul.push_back(jd_);
         }
-        warm1.push_back(gdesc<T>(B.G[i], pp_, B.W[i], pp_, B.T1[i], pp_, pi, pi, pi, B.svt_on + i));
-        warm2.push_back(gdesc<T>(B.W[i], pp_, B.T1[i], pp_, B.G[i], pp_, pi, pi, pi, B.svt_on + i));
-        GemmDesc<T> hm = gdesc<T>(B.W[i], pp_, B.W[i], pp_, B.H[i], pp_, pi, pi, pi, B.act + i);
-        hm.kscale = B.h[i];
-        hmat.push_back(hm);
+        orth1.push_back(gdesc<T>(B.W[i], pp_, B.W[i], pp_, B.T1[i], pp_, pi, pi, pi, B.svt_on + i));
+        orth2.push_back(gdesc<T>(B.W[i], pp_, B.T1[i], pp_, B.H[i], pp_, pi, pi, pi, B.svt_on + i));
         tmul.push_back(gdesc<T>(B.U, m, B.P + c0 * m, m, B.Tt + c0 * r, r, r, l, (int)m, B.act + i));
         mzmul.push_back(gdesc<T>(B.US, m, B.Zt + c0 * r, r, B.MZ + c0 * m, m, (int)m, l, r, B.act + i));
         GemmDesc<T> ex = gdesc<T>(B.V, n, B.D + c0 * r, r, nullptr, 0, (int)n, l, r, B.need_exact + i);
         ex.absmax = B.r2x + i;
         exact.push_back(ex);
     }
-    const int S_GT = gram_tall.empty() ? -1 : add_set(true, false, gram_tall);
-    const int S_GW = gram_wide.empty() ? -1 : add_set(false, true, gram_wide);
-    const int S_W1 = add_set(false, false, warm1);
-    const int S_W2 = add_set(true, false, warm2);
-    const int S_H = add_set(false, true, hmat);
-    const int S_JT = j_tall.empty() ? -1 : add_set(false, false, j_tall);
-    const int S_JW = j_wide.empty() ? -1 : add_set(false, false, j_wide);
+    const int S_XT = xw_tall.empty() ? -1 : add_set(false, false, xw_tall);
+    const int S_XW = xw_wide.empty() ? -1 : add_set(true, false, xw_wide);
+    const int S_J = add_set(false, true, jmul);
     const int S_T = add_set(true, false, tmul);
     const int S_MZ = add_set(false, false, mzmul);
     const int S_EX = add_set(false, false, exact);
-    if (gh.size() > 16 * (size_t)t + 16) return LRR_ERR_INVALID;
+    const int S_O1 = add_set(true, false, orth1);
+    const int S_O2 = add_set(false, false, orth2);
+    if (gh.size() + 10 > 16 * (size_t)t + 16) return LRR_ERR_INVALID;
     LRR_CUDA_TRY(cudaMemcpyAsync(B.gd, gh.data(), sizeof(GemmDesc<T>) * gh.size(), cudaMemcpyHostToDevice, s));
     auto run_set = [&](int si) -> cudaError_t {
         if (si < 0) return cudaSuccess;
@@ -415,6 +492,8 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     };
 
     // ---- state
+    prof.launches += 1 + (int64_t)t;
+    prof.calls[LRR_PH_SETUP] += 1 + (int64_t)t;
     k::gather_cols<T, Tin><<<dim3(grid1(m), (unsigned)std::min<int64_t>(n, 65535)), 256, 0, s>>>(M, p->ldm, B.perm, m, n, B.C);
     LRR_CUDA_TRY(cudaMemcpyAsync(B.P, B.C, sizeof(T) * m * n, cudaMemcpyDeviceToDevice, s));
     LRR_CUDA_TRY(cudaMemsetAsync(B.E, 0, sizeof(T) * m * n, s));
@@ -423,10 +502,12 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         T* zs[5] = {B.Zt, B.Jt, B.Y2t, B.A, B.D};
         for (T* x : zs) { LRR_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * r * n, s)); }
     }
-    for (int i = 0; i < t; ++i) {
-        k::init_padded<T><<<grid1((int64_t)ppv[i] * ppv[i]), 256, 0, s>>>(B.G[i], pv[i], ppv[i], T(-1), 0);
+    for (int i = 0; i < t; ++i)
         k::init_padded<T><<<grid1((int64_t)ppv[i] * ppv[i]), 256, 0, s>>>(B.W[i], pv[i], ppv[i], T(1), 1);
-    }
+    LRR_CUDA_TRY(cudaMemsetAsync(B.afro, 0, sizeof(double) * t, s));
+    for (int i = 0; i < t; ++i)   // the SVT reconstruction reads it with zero weights before the first SVD
+        LRR_CUDA_TRY(cudaMemsetAsync(B.T1[i], 0, sizeof(T) * (size_t)ppv[i] * ppv[i], s));
+    LRR_CUDA_TRY(cudaMemsetAsync(B.jsweeps, 0, sizeof(int) * t, s));
     std::vector<double> mu0((size_t)t, o->mu0);
     LRR_CUDA_TRY(cudaMemcpyAsync(B.mu, mu0.data(), sizeof(double) * t, cudaMemcpyHostToDevice, s));
     LRR_CUDA_TRY(cudaMemcpyAsync(B.mu_fin, mu0.data(), sizeof(double) * t, cudaMemcpyHostToDevice, s));
@@ -439,35 +520,57 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     LRR_CUDA_TRY(cudaMemsetAsync(B.resid, 0, sizeof(double) * 2 * t, s));
 
     const int sweeps = o->jacobi_sweeps > 0 ? o->jacobi_sweeps : 12;
-    const T jtol = sizeof(T) == 8 ? T(1e-13) : T(4e-6);
+    const T jtol = sizeof(T) == 8 ? T(1e-13) : T(2e-6);
     const unsigned wgrid_n = (unsigned)((n * 32 + 255) / 256);
+    const int nset = [&](int si) { return si < 0 ? 0 : 1; }(0);
+    (void)nset;
+    auto nl = [&](int si) -> int64_t { return si < 0 ? 0 : 1; };
+    const int64_t jac_launches = 1 + (int64_t)sweeps * ((max_pp / jacobi_bs<T>() - 1) + 1);
     auto iteration = [&]() -> int {
+        prof.iterations += 1;
         // J-step: SVT of A = Zt + Y2t/mu through the Gram eigendecomposition
-        LRR_CUDA_TRY(run_set(S_GT));
-        LRR_CUDA_TRY(run_set(S_GW));
-        k::svt_gate<T><<<t, 256, 0, s>>>(B.Gp, B.pv, B.ppv, B.act, B.mu, B.svt_on, B.jscale, t);
-        LRR_CUDA_TRY(run_set(S_W1));
-        LRR_CUDA_TRY(run_set(S_W2));
-        LRR_CUDA_TRY(jacobi_sweeps<T>(B.jd, t, max_pp, sweeps, jtol, s));
-        k::svt_weights<T><<<t, 256, 0, s>>>(B.Gp, B.hp, B.pv, B.ppv, B.act, B.svt_on, B.mu, B.rank_cur, t);
-        LRR_CUDA_TRY(run_set(S_H));
-        LRR_CUDA_TRY(run_set(S_JT));
-        LRR_CUDA_TRY(run_set(S_JW));
+        prof.begin();
+        k::svt_gate<T><<<ceil_div(t, 128), 128, 0, s>>>(B.act, B.afro, B.mu, B.svt_on, B.jscale, t);
+        LRR_CUDA_TRY(run_set(S_XT));
+        LRR_CUDA_TRY(run_set(S_XW));
+        prof.end(LRR_PH_GRAM, 1 + nl(S_XT) + nl(S_XW));
+        prof.begin();
+        k::col_norm_max<T><<<t, 256, 0, s>>>(B.jd, B.svt_on, B.jscale, t);
+        LRR_CUDA_TRY(osj_sweeps<T>(B.jd, t, max_pp, sweeps, jtol, B.jsweeps, s));
+        prof.end(LRR_PH_JACOBI, jac_launches + 1);
+        prof.begin();
+        k::svt_weights<T><<<t, 256, 0, s>>>(B.jd, B.hp, B.act, B.svt_on, B.mu, B.rank_cur, t);
+        // W^T W and W (W^T W): first-order inverse for J, Newton-Schulz for the warm start
+        LRR_CUDA_TRY(run_set(S_O1));
+        LRR_CUDA_TRY(run_set(S_O2));
+        k::ns_orth<T><<<dim3(64, (unsigned)t), 256, 0, s>>>(B.Wp, B.Hp, B.T1p, B.pv, B.ppv, B.svt_on, t);
+        LRR_CUDA_TRY(run_set(S_J));
+        prof.end(LRR_PH_SVT_APPLY, 5);
         // Z-step
+        prof.begin();
         LRR_CUDA_TRY(run_set(S_T));
+        prof.end(LRR_PH_ZGEMM, 1);
+        prof.begin();
         k::z_update<T><<<wgrid_n, 256, 0, s>>>(r, n, B.colblk, B.act, B.mu, o->rho, o->mu_max, B.Tt, B.Jt, B.Y2t,
-                                               B.Zt, B.D, B.A, B.sig, B.dinv, B.dmax);
+                                               B.Zt, B.D, B.A, B.sig, B.dinv, B.dmax, B.afro);
+        prof.end(LRR_PH_ZUPDATE, 1);
         // E-step, residuals, duals
+        prof.begin();
         LRR_CUDA_TRY(run_set(S_MZ));
+        prof.end(LRR_PH_MZGEMM, 1);
+        prof.begin();
         k::e_update<T><<<wgrid_n, 256, 0, s>>>(m, n, B.colblk, B.act, B.mu, o->rho, o->mu_max, o->lambda, B.C,
                                                B.MZ, B.Y1, B.E, B.P, B.r1);
-        k::stop_part1<T><<<ceil_div(t, 128), 128, 0, s>>>(t, B.act, B.r1, B.dmax, nu_h, o->eps, B.need_exact,
+        prof.end(LRR_PH_EUPDATE, 1);
+        prof.begin();
+        k::stop_part1<T><<<ceil_div(t, 128), 128, 0, s>>>(t, B.act, B.r1, B.dmax, nu_h, 1.0 / std::sqrt((double)n), o->eps, B.need_exact,
                                                           B.conv_bound);
         LRR_CUDA_TRY(run_set(S_EX));
         k::stop_part2<T><<<ceil_div(t, 128), 128, 0, s>>>(t, B.act, B.iters, B.mu, o->rho, o->mu_max, o->eps,
                                                           o->max_iter, B.r1, B.dmax, B.r2x, B.need_exact,
                                                           B.conv_bound, nu_h, B.resid, B.rank_cur, B.rank_fin,
-                                                          B.conv, B.mu_fin);
+                                                          B.conv, B.mu_fin, B.afro);
+        prof.end(LRR_PH_STOP, 3);
         LRR_CUDA_TRY(cudaGetLastError());
         return LRR_OK;
     };
@@ -481,8 +584,11 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
                 const int rc = iteration();
                 if (rc != LRR_OK) return rc;
             }
+            prof.begin();
             LRR_CUDA_TRY(cudaMemcpyAsync(ah.data(), B.act, sizeof(int) * t, cudaMemcpyDeviceToHost, s));
+            prof.end(LRR_PH_HOST, 0);
             LRR_CUDA_TRY(cudaStreamSynchronize(s));
+            prof.flush();
             if (std::none_of(ah.begin(), ah.end(), [](int v) { return v != 0; })) break;
         }
         return LRR_OK;
@@ -563,6 +669,12 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     if (res && res->S)
         k::scatter_cols<T><<<dim3(grid1(m), (unsigned)std::min<int64_t>(n, 65535)), 256, 0, s>>>(B.E, m, n, B.perm, static_cast<T*>(res->S));
     LRR_CUDA_TRY(cudaEventRecord(ev[3], s));
+    {
+        int64_t cl = (res && res->Z ? 1 : 0) + (res && res->S ? 1 : 0);
+        if (dfc && t > 1) cl += 2 + (tall[0] ? 1 : 0) + (k1 > 0 ? 3 * 3 + 3 : 0);
+        prof.launches += cl;
+        prof.calls[LRR_PH_COMBINE] += cl;
+    }
 
     std::vector<int> iters_h((size_t)t), conv_h((size_t)t);
     std::vector<double> resid_h((size_t)2 * t);
@@ -578,6 +690,19 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
             res->ranks[1] = k1;
             for (int i = 0; i < t; ++i) res->ranks[2 + i] = rank_fin[i];
         }
+        if (res->stats) {
+            lrr_stats& st = *res->stats;
+            std::memset(&st, 0, sizeof(st));
+            prof.flush();
+            for (int i = 0; i < LRR_NPHASE; ++i) { st.phase_ms[i] = prof.ms[i]; st.phase_launches[i] = prof.calls[i]; }
+            float a = 0, c = 0;
+            cudaEventElapsedTime(&a, ev[0], ev[1]);
+            cudaEventElapsedTime(&c, ev[2], ev[3]);
+            st.phase_ms[LRR_PH_SETUP] = a;
+            st.phase_ms[LRR_PH_COMBINE] = c;
+            st.launches = prof.launches;
+            st.iterations = prof.iterations;
+        }
         if (res->timings_ms) {
             float a = 0, b2 = 0, c = 0;
             cudaEventElapsedTime(&a, ev[0], ev[1]);
@@ -588,6 +713,101 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     }
     for (int i = 0; i < t; ++i)
         if (!conv_h[i]) return LRR_NOT_CONVERGED;
+    return LRR_OK;
+}
+
+
+// Stand-alone singular-value thresholding with the solver's own SVT kernels
+// (cold start W = I).  Scratch is taken with cudaMallocAsync on the stream.
+template <typename T>
+int svt_impl(const T* A, int64_t rows, int64_t cols, int64_t lda, double tau, T* J, int64_t ldj, int32_t* rank_out,
+             cudaStream_t s) {
+    constexpr int B2 = 2 * jacobi_bs<T>();
+    const bool tall = cols <= rows;
+    const int p = (int)std::min(rows, cols);
+    const int L = (int)(tall ? rows : cols);
+    const int pp = round_up(p, B2);
+    Arena sz(nullptr);
+    auto lay = [&](Arena& a, T** X, T** W, T** H, T** T1, T** h, int** ints, double** dbl, OsjDesc<T>** od,
+                   GemmDesc<T>** gd, T** Wp, T** Hp, T** hp, T** scl, T** off, T** T1p) {
+        *X = a.take<T>((size_t)L * p);
+        *W = a.take<T>((size_t)pp * pp);
+        *H = a.take<T>((size_t)pp * pp);
+        *T1 = a.take<T>((size_t)pp * pp);
+        *h = a.take<T>(pp);
+        *ints = a.take<int>(16);
+        *dbl = a.take<double>(4);
+        *od = a.take<OsjDesc<T>>(1);
+        *gd = a.take<GemmDesc<T>>(8);
+        *Wp = reinterpret_cast<T*>(a.take<T*>(1));
+        *Hp = reinterpret_cast<T*>(a.take<T*>(1));
+        *hp = reinterpret_cast<T*>(a.take<T*>(1));
+        *scl = a.take<T>(1);
+        *off = a.take<T>(1);
+        *T1p = reinterpret_cast<T*>(a.take<T*>(1));
+    };
+    T *X, *W, *H, *T1, *h, *Wp, *Hp, *hp, *scl, *off, *T1p;
+    int* ints;
+    double* dbl;
+    OsjDesc<T>* od;
+    GemmDesc<T>* gd;
+    lay(sz, &X, &W, &H, &T1, &h, &ints, &dbl, &od, &gd, &Wp, &Hp, &hp, &scl, &off, &T1p);
+    void* mem = nullptr;
+    if (cudaMallocAsync(&mem, sz.off + kAlign, s) != cudaSuccess) return LRR_ERR_CUDA;
+    struct Free {
+        void* p; cudaStream_t s;
+        ~Free() { if (p) cudaFreeAsync(p, s); }
+    } guard{mem, s};
+    Arena a(mem);
+    lay(a, &X, &W, &H, &T1, &h, &ints, &dbl, &od, &gd, &Wp, &Hp, &hp, &scl, &off, &T1p);
+    int* act = ints;          // [0]
+    int* on = ints + 1;       // [1]
+    int* rk = ints + 2;       // [2]
+    int* done = ints + 3;     // [3]
+    int* swp = ints + 4;      // [4]
+    double* mu = dbl;
+    const int one[2] = {1, 1};
+    const double mud = 1.0 / tau;
+    LRR_CUDA_TRY(cudaMemcpyAsync(act, one, sizeof(int) * 2, cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemsetAsync(swp, 0, sizeof(int), s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(mu, &mud, sizeof(double), cudaMemcpyHostToDevice, s));
+    k::init_padded<T><<<grid1((int64_t)pp * pp), 256, 0, s>>>(W, p, pp, T(1), 1);
+    T* ptrs[4] = {W, H, h, T1};
+    LRR_CUDA_TRY(cudaMemcpyAsync(T1p, &ptrs[3], sizeof(T*), cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(Wp, &ptrs[0], sizeof(T*), cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(Hp, &ptrs[1], sizeof(T*), cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(hp, &ptrs[2], sizeof(T*), cudaMemcpyHostToDevice, s));
+    const int pvals[2] = {p, pp};
+    int* pv = ints + 8;
+    int* ppv = ints + 9;
+    LRR_CUDA_TRY(cudaMemcpyAsync(pv, &pvals[0], sizeof(int), cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(ppv, &pvals[1], sizeof(int), cudaMemcpyHostToDevice, s));
+    OsjDesc<T> d{};
+    d.X = X; d.W = W; d.done = done; d.off = off; d.active = on; d.scale = scl;
+    d.ldx = L; d.ldw = pp; d.L = L; d.p = p; d.pp = pp;
+    LRR_CUDA_TRY(cudaMemcpyAsync(od, &d, sizeof(d), cudaMemcpyHostToDevice, s));
+    GemmDesc<T> g[5];
+    if (tall) g[0] = gdesc<T>(A, lda, W, pp, X, L, L, p, p, nullptr);          // X = A W
+    else g[0] = gdesc<T>(A, lda, W, pp, X, L, L, p, p, nullptr);               // X = A^T W
+    g[1] = gdesc<T>(W, pp, W, pp, T1, pp, p, p, p, nullptr);                   // W^T W
+    g[2] = gdesc<T>(W, pp, T1, pp, H, pp, p, p, p, nullptr);                   // W (W^T W)
+    if (tall) g[3] = gdesc<T>(X, L, T1, pp, J, ldj, (int)rows, (int)cols, p, nullptr);   // J = X h W^{-1}
+    else g[3] = gdesc<T>(T1, pp, X, L, J, ldj, (int)rows, (int)cols, p, nullptr);        // J = W^{-T} h X^T
+    g[3].kscale = h;
+    LRR_CUDA_TRY(cudaMemcpyAsync(gd, g, sizeof(g), cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(gemm_grouped<T>(gd, 1, !tall, false, L, p, s));
+    k::col_norm_max<T><<<1, 256, 0, s>>>(od, on, scl, 1);
+    LRR_CUDA_TRY(osj_sweeps<T>(od, 1, pp, 40, sizeof(T) == 8 ? T(1e-13) : T(2e-6), swp, s));
+    k::svt_weights<T><<<1, 256, 0, s>>>(od, reinterpret_cast<T* const*>(hp), act, on, mu, rk, 1);
+    LRR_CUDA_TRY(gemm_grouped<T>(gd + 1, 1, true, false, p, p, s));
+    LRR_CUDA_TRY(gemm_grouped<T>(gd + 2, 1, false, false, p, p, s));
+    k::ns_orth<T><<<dim3(64, 1), 256, 0, s>>>(reinterpret_cast<T* const*>(Wp), reinterpret_cast<T* const*>(Hp),
+                                              reinterpret_cast<T* const*>(T1p), pv, ppv, on, 1);
+    LRR_CUDA_TRY(gemm_grouped<T>(gd + 3, 1, false, true, (int)rows, (int)cols, s));
+    int rk_h = 0;
+    LRR_CUDA_TRY(cudaMemcpyAsync(&rk_h, rk, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LRR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (rank_out) *rank_out = rk_h;
     return LRR_OK;
 }
 
@@ -630,6 +850,20 @@ int lrr_solve(const lrr_problem* p, const lrr_options* o, void* ws, size_t wsb, 
 
 int dfc_lrr_solve(const lrr_problem* p, const lrr_options* o, void* ws, size_t wsb, lrr_result* r, void* stream) {
     return lrr::dispatch(p, o, ws, wsb, r, stream, true);
+}
+
+int lrr_svt(const void* A, int64_t rows, int64_t cols, int64_t lda, double tau, void* J, int64_t ldj,
+            int32_t precision, int32_t* rank, void* stream) {
+    if (!A || !J || rows < 1 || cols < 1 || lda < rows || ldj < rows || !(tau > 0)) return LRR_ERR_INVALID;
+    if (rows > (1 << 16) || cols > (1 << 16)) return LRR_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == LRR_PREC_F64)
+        return lrr::svt_impl<double>(static_cast<const double*>(A), rows, cols, lda, tau, static_cast<double*>(J), ldj,
+                                     rank, s);
+    if (precision == LRR_PREC_F32)
+        return lrr::svt_impl<float>(static_cast<const float*>(A), rows, cols, lda, tau, static_cast<float*>(J), ldj,
+                                    rank, s);
+    return LRR_ERR_UNSUPPORTED;
 }
 
 void lrr_default_options(lrr_options* o) {

@@ -106,6 +106,25 @@ def algorithmic_work(w, rank_M, iters):
     # Gram: tall blocks A^T A (2 l^2 r), wide A A^T (2 r^2 l)
     g = np.where(l <= r, 2.0 * l * l * r, 2.0 * r * r * l)
     out["gram"] = {"flops": float(np.sum(it * g)), "bytes": float(np.sum(it * fb * r * l))}
+    return _elementwise(out, w, r, m, l, it, fb)
+
+
+def jacobi_work(w, rank_M, sweeps_total):
+    """Algorithmic flops of the one-sided block-Jacobi sweeps: per sweep and
+    block, the pivot Grams cost 4 L p^2 and the rotations of X and W
+    4 (L + p) p^2 (round-robin pairing of p/b blocks of width b: every round
+    forms and applies p/(2b) Grams of width 2b), i.e. 8 L p^2 + 4 p^3 with
+    L = rank(M), p = l for a tall block and L = l, p = rank(M) for a wide one.
+    The sweeps are spread evenly over the blocks."""
+    r = rank_M
+    l = np.diff(w.offsets).astype(np.float64)
+    L = np.where(l <= r, r, l)
+    p = np.where(l <= r, l, r)
+    per_sweep = 8 * L * p * p + 4 * p ** 3
+    return float(sweeps_total / len(l) * per_sweep.sum())
+
+
+def _elementwise(out, w, r, m, l, it, fb):
     # element-wise kernels: bytes moved per block-iteration
     out["zupdate"] = {"flops": float(np.sum(it * 9 * r * l)), "bytes": float(np.sum(it * fb * r * l * 7))}
     out["eupdate"] = {"flops": float(np.sum(it * 14 * m * l)), "bytes": float(np.sum(it * fb * m * l * 8))}
@@ -189,6 +208,8 @@ def bench_ours(args, rank, world):
     # ---- roofline of the dominant kernel family
     peaks, src = _peaks()
     work = algorithmic_work(w, res.rank_M, res.iters)
+    sweeps = float(np.mean([r_.stats["svt_sweeps"] for r_ in results]))
+    work["jacobi"] = {"flops": jacobi_work(w, res.rank_M, sweeps), "bytes": None}
     loop_phases = [k for k in binding.PHASES if k not in ("setup", "combine", "host")]
     dom = max(loop_phases, key=lambda k: phase_ms[k])
     sm_max = peaks.get("sm_max_mhz", 2070.0)
@@ -224,6 +245,7 @@ def bench_ours(args, rank, world):
         "block_iters_per_s": iters_total / solve_s,
         "iters": {"max": int(np.max(res.iters)), "sum": iters_total, "per_block": res.iters.tolist()},
         "phase_ms": phase_ms, "phase_launches": phase_launch,
+        "svt": {"sweeps": res.stats["svt_sweeps"], "calls": res.stats["svt_calls"]},
         "roofline": roof,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches * args.steps,

@@ -112,6 +112,8 @@ typedef struct {
     int64_t phase_launches[LRR_NPHASE];
     int64_t launches;           /* kernels launched by the call                       */
     int64_t iterations;         /* ALM iterations launched (all blocks together)      */
+    int64_t svt_sweeps;         /* Jacobi sweeps run, summed over blocks and iterations */
+    int64_t svt_calls;          /* SVTs that needed an SVD, summed over blocks          */
 } lrr_stats;
 
 typedef struct {

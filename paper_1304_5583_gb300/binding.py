@@ -43,7 +43,8 @@ PHASES = ("setup", "gram", "warm", "jacobi", "svt_apply", "zgemm", "zupdate", "m
 
 class LrrStats(ctypes.Structure):
     _fields_ = [("phase_ms", ctypes.c_double * NPHASE), ("phase_launches", ctypes.c_int64 * NPHASE),
-                ("launches", ctypes.c_int64), ("iterations", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("iterations", ctypes.c_int64), ("svt_sweeps", ctypes.c_int64),
+                ("svt_calls", ctypes.c_int64)]
 
 
 class LrrResult(ctypes.Structure):
@@ -183,7 +184,8 @@ def _solve(entry: str, M, perm, offsets, opts: LrrOptions, want_Z=True, want_S=T
                        block_ranks=ranks[2:].copy(), timings_ms=tim, status=int(code),
                        stats={"phase_ms": dict(zip(PHASES, list(st.phase_ms))),
                               "phase_launches": dict(zip(PHASES, list(st.phase_launches))),
-                              "launches": int(st.launches), "iterations": int(st.iterations)})
+                              "launches": int(st.launches), "iterations": int(st.iterations),
+                              "svt_sweeps": int(st.svt_sweeps), "svt_calls": int(st.svt_calls)})
 
 
 def dfc_lrr_solve(M, perm, offsets, opts: LrrOptions, **kw) -> SolveResult:

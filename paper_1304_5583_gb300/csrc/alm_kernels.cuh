@@ -75,11 +75,12 @@ __global__ void init_padded(T* __restrict__ G, int p, int pp, T diag, int eye) {
 // The Z-step kernel of the same iteration then accumulates the next value.
 template <typename T>
 __global__ void svt_gate(const int* __restrict__ act, double* __restrict__ afro, const double* __restrict__ mu,
-                         int* __restrict__ svt_on, T* __restrict__ scale, int nblk) {
+                         int* __restrict__ svt_on, T* __restrict__ scale, int* __restrict__ calls, int nblk) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nblk) return;
     const double tau = 1.0 / mu[b];
     svt_on[b] = (act[b] && afro[b] > tau * tau) ? 1 : 0;
+    if (svt_on[b]) calls[b] += 1;
     if (act[b]) {
         scale[b] = (T)afro[b];
         afro[b] = 0.0;

@@ -61,8 +61,10 @@ struct OsjDesc {
     T* off;
     const int* active;
     const T* scale;     // largest squared column norm of X
+    const double* mu;   // SVT threshold is 1/mu (nullptr: measure every pair)
     int64_t ldx, ldw;
     int L, p, pp;
+    int strict;         // 1: resolve pairs straddling tau to angle tol (C-step block)
 };
 
 template <typename T>

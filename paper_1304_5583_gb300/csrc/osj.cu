@@ -12,6 +12,8 @@
 // A matrix is converged once a whole sweep saw every pivot Gram with
 // max |s_ij| / sqrt(s_ii s_jj) <= tol; then the squared column norms of X are
 // the eigenvalues of the Gram A^T A (or A A^T) and W holds its eigenvectors.
+#include <type_traits>
+
 #include "common.cuh"
 #include "inner_jacobi.cuh"
 #include "kernels.cuh"
@@ -20,6 +22,9 @@ namespace lrr {
 namespace {
 
 constexpr int NT = 256;
+// pivot Gram chunk sums accumulated in float64 (measured: no accuracy gain over
+// float32 once the block rotations are re-orthonormalised, so off)
+constexpr bool kGramF64 = false;
 
 __device__ __forceinline__ int pcol(int i, int a, int c, int b) { return i < b ? a * b + i : c * b + (i - b); }
 
@@ -50,16 +55,13 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
     const T noise = T(64) * num<T>::eps();
     const T floor2 = noise * noise * (*d.scale) + num<T>::tiny();
 
-    // 1. pivot Gram S = X_P^T X_P from the columns of X.  Partial sums over
-    //    B2-row chunks are formed in T and added into float64 accumulators:
-    //    a float32 sum over all L rows would leave noise ~sqrt(L) eps in every
-    //    scaled entry, which caps how orthogonal the columns can be made; with
-    //    chunked float64 accumulation it drops to ~sqrt(B2) eps / sqrt(L/B2).
-    double acc[TI][TI];
+    // 1. pivot Gram S = X_P^T X_P from the columns of X, in B2-row chunks
+    using Acc = typename std::conditional<kGramF64, double, T>::type;
+    Acc acc[TI][TI];
 #pragma unroll
     for (int u = 0; u < TI; ++u)
 #pragma unroll
-        for (int v = 0; v < TI; ++v) acc[u][v] = 0.0;
+        for (int v = 0; v < TI; ++v) acc[u][v] = Acc(0);
     for (int r0 = 0; r0 < d.L; r0 += B2) {
         for (int e = t; e < B2 * B2; e += NT) {
             const int rr = e % B2, cc = e / B2;
@@ -85,7 +87,7 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
 #pragma unroll
         for (int u = 0; u < TI; ++u)
 #pragma unroll
-            for (int v = 0; v < TI; ++v) acc[u][v] += (double)part[u][v];
+            for (int v = 0; v < TI; ++v) acc[u][v] += (Acc)part[u][v];
         __syncthreads();
     }
 #pragma unroll
@@ -98,21 +100,45 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
         }
     __syncthreads();
 
-    // 2. convergence measure before rotating (noise columns excluded)
+    // 2. convergence measure before rotating: how much the rotation this pair
+    //    still needs could change J = U max(Sigma - tau, 0) V^T, relative to
+    //    the largest singular value.  For columns of norms a, b, an unresolved
+    //    rotation of tangent t moves J by about t |f(a) - f(b)| (f(s) =
+    //    max(s - tau, 0) is 1-Lipschitz, so |a - b| bounds it), plus tau theta
+    //    when both lie above tau (the pair then enters J as A - tau U V^T and
+    //    theta = |s_ij| / (a b) is its angle defect).  Pairs whose norms
+    //    satisfy a^2 + b^2 <= tau^2 have every singular value below tau and
+    //    are removed by the SVT whatever their rotation; noise columns (below
+    //    the rounding floor) are skipped.  A `strict` matrix (the block whose
+    //    kept left singular subspace the C step projects onto) also needs that
+    //    subspace itself: pairs straddling tau are measured by t alone.
+    const T tau = d.mu ? (T)(1.0 / *d.mu) : T(0);
+    const T tau2 = tau * tau;
+    const T inv_smax = T(1) / (sqrt(*d.scale) + num<T>::tiny());
     T offm = T(0);
     for (int e = t; e < B2 * B2; e += NT) {
         const int i = e % B2, j = e / B2;
-        if (i < j && S[i][i] > floor2 && S[j][j] > floor2)
-            offm = fmax(offm, fabs(S[i][j]) / sqrt(S[i][i] * S[j][j]));
+        const T sii = S[i][i], sjj = S[j][j];
+        if (i < j && sii > floor2 && sjj > floor2 && sii + sjj > tau2) {
+            const T sij = fabs(S[i][j]);
+            const T a = sqrt(sii), bb = sqrt(sjj);
+            const T hd = T(0.5) * fabs(sii - sjj);
+            const T tn = sij / (hd + sqrt(hd * hd + sij * sij) + num<T>::tiny());
+            T mm;
+            if (a > tau && bb > tau) mm = tn * fabs(a - bb) + tau * sij / (a * bb);
+            else if (a > tau || bb > tau) mm = d.strict ? tn * (*d.scale > 0 ? sqrt(*d.scale) : T(1)) : tn * fabs(a - bb);
+            else mm = tn * (sqrt(sii + sjj) - tau);
+            offm = fmax(offm, mm * inv_smax);
+        }
     }
     offm = warp_max(offm);
     if ((t & 31) == 0) red[t >> 5] = offm;
     __syncthreads();
-    if (t == 0) {
-        T mx = T(0);
-        for (int w = 0; w < NT / 32; ++w) mx = fmax(mx, red[w]);
-        atomic_max_nonneg(d.off, mx);
-    }
+    T mx = T(0);
+    for (int w = 0; w < NT / 32; ++w) mx = fmax(mx, red[w]);
+    if (t == 0) atomic_max_nonneg(d.off, mx);
+    // a pivot already orthogonal to a few eps needs no rotation
+    if (mx <= T(16) * num<T>::eps()) return;
 
     // 3. rotate the pivot Gram to diagonal form; rotations that only mix noise
     //    columns (|s_pq| below floor2) do not keep the inner sweeps going
@@ -225,8 +251,8 @@ __global__ void osj_check(const OsjDesc<T>* __restrict__ descs, int nmat, T tol,
     if (d.active && *d.active == 0) return;
     if (*d.done == 0) {
         if (sweeps_run) sweeps_run[i] += 1;
-        // the pivot Grams are accumulated in float64 over float32 chunk sums, so
-        // their noise is a few eps relative to sqrt(s_ii s_jj)
+        // scaled off-diagonals below ~64 eps are at the rounding level of the
+        // fresh pivot Grams
         const T t_eff = fmax(tol, T(64) * num<T>::eps());
         if (*d.off <= t_eff) *d.done = 1;
     }

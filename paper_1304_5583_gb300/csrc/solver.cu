@@ -99,6 +99,7 @@ struct Buffers {
     OsjDesc<T>* jd;
     double* afro;
     int* jsweeps;
+    int* svtcalls;
     T** Gp;
     T** hp;
     T** Wp;
@@ -189,6 +190,7 @@ Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector
     b.jd = a.take<OsjDesc<T>>(t);
     b.afro = a.take<double>(t);
     b.jsweeps = a.take<int>(t);
+    b.svtcalls = a.take<int>(t);
     b.Gp = a.take<T*>(t);
     b.hp = a.take<T*>(t);
     b.Wp = a.take<T*>(t);
@@ -433,6 +435,8 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         j.L = tall[i] ? r : blk[i].l;
         j.W = B.W[i]; j.ldw = ppv[i]; j.p = pv[i]; j.pp = ppv[i];
         j.done = B.jdone + i; j.off = B.joff + i; j.active = B.svt_on + i; j.scale = B.jscale + i;
+        j.mu = B.mu + i;
+        j.strict = (dfc && t > 1 && i == 0) ? 1 : 0;
     }
     LRR_CUDA_TRY(cudaMemcpyAsync(B.jd, jdh.data(), sizeof(OsjDesc<T>) * t, cudaMemcpyHostToDevice, s));
 
@@ -508,6 +512,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     for (int i = 0; i < t; ++i)   // the SVT reconstruction reads it with zero weights before the first SVD
         LRR_CUDA_TRY(cudaMemsetAsync(B.T1[i], 0, sizeof(T) * (size_t)ppv[i] * ppv[i], s));
     LRR_CUDA_TRY(cudaMemsetAsync(B.jsweeps, 0, sizeof(int) * t, s));
+    LRR_CUDA_TRY(cudaMemsetAsync(B.svtcalls, 0, sizeof(int) * t, s));
     std::vector<double> mu0((size_t)t, o->mu0);
     LRR_CUDA_TRY(cudaMemcpyAsync(B.mu, mu0.data(), sizeof(double) * t, cudaMemcpyHostToDevice, s));
     LRR_CUDA_TRY(cudaMemcpyAsync(B.mu_fin, mu0.data(), sizeof(double) * t, cudaMemcpyHostToDevice, s));
@@ -530,7 +535,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         prof.iterations += 1;
         // J-step: SVT of A = Zt + Y2t/mu through the Gram eigendecomposition
         prof.begin();
-        k::svt_gate<T><<<ceil_div(t, 128), 128, 0, s>>>(B.act, B.afro, B.mu, B.svt_on, B.jscale, t);
+        k::svt_gate<T><<<ceil_div(t, 128), 128, 0, s>>>(B.act, B.afro, B.mu, B.svt_on, B.jscale, B.svtcalls, t);
         LRR_CUDA_TRY(run_set(S_XT));
         LRR_CUDA_TRY(run_set(S_XW));
         prof.end(LRR_PH_GRAM, 1 + nl(S_XT) + nl(S_XW));
@@ -702,6 +707,10 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
             st.phase_ms[LRR_PH_COMBINE] = c;
             st.launches = prof.launches;
             st.iterations = prof.iterations;
+            std::vector<int> sw((size_t)t), sc((size_t)t);
+            cudaMemcpy(sw.data(), B.jsweeps, sizeof(int) * t, cudaMemcpyDeviceToHost);
+            cudaMemcpy(sc.data(), B.svtcalls, sizeof(int) * t, cudaMemcpyDeviceToHost);
+            for (int i = 0; i < t; ++i) { st.svt_sweeps += sw[i]; st.svt_calls += sc[i]; }
         }
         if (res->timings_ms) {
             float a = 0, b2 = 0, c = 0;
@@ -783,8 +792,8 @@ int svt_impl(const T* A, int64_t rows, int64_t cols, int64_t lda, double tau, T*
     LRR_CUDA_TRY(cudaMemcpyAsync(pv, &pvals[0], sizeof(int), cudaMemcpyHostToDevice, s));
     LRR_CUDA_TRY(cudaMemcpyAsync(ppv, &pvals[1], sizeof(int), cudaMemcpyHostToDevice, s));
     OsjDesc<T> d{};
-    d.X = X; d.W = W; d.done = done; d.off = off; d.active = on; d.scale = scl;
-    d.ldx = L; d.ldw = pp; d.L = L; d.p = p; d.pp = pp;
+    d.X = X; d.W = W; d.done = done; d.off = off; d.active = on; d.scale = scl; d.mu = mu;
+    d.ldx = L; d.ldw = pp; d.L = L; d.p = p; d.pp = pp; d.strict = 1;
     LRR_CUDA_TRY(cudaMemcpyAsync(od, &d, sizeof(d), cudaMemcpyHostToDevice, s));
     GemmDesc<T> g[5];
     if (tall) g[0] = gdesc<T>(A, lda, W, pp, X, L, L, p, p, nullptr);          // X = A W

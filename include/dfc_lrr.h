@@ -157,6 +157,16 @@ LRR_API int dfc_lrr_solve(const lrr_problem* p, const lrr_options* o, void* work
 LRR_API int lrr_svt(const void* A, int64_t rows, int64_t cols, int64_t lda, double tau, void* J, int64_t ldj,
                     int32_t precision, int32_t* rank, void* stream);
 
+/* The tensor-core product of the mixed-precision iteration on its own:
+ * C = A B with A (M x K) and B (K x N) bf16, both stored K-major (element
+ * (m, k) at A[k + m lda], element (k, n) at B[k + n ldb]), lda and ldb
+ * multiples of 8, A and B 16-byte aligned; C float, column-major, ldc >= M.
+ * All device pointers; the call synchronises `stream` and returns
+ * LRR_ERR_CUDA if a launch failed or a wait inside the kernel timed out.
+ * Scratch: one int taken with cudaMallocAsync. */
+LRR_API int lrr_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
+                          int64_t N, int64_t K, void* stream);
+
 /* Fill `o` with the defaults above (lambda = 0.1). */
 LRR_API void lrr_default_options(lrr_options* o);
 

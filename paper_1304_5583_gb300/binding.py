@@ -21,7 +21,8 @@ LRR_PREC_F64, LRR_PREC_F32, LRR_PREC_MIXED = 0, 1, 2
 PRECISIONS = {"f64": LRR_PREC_F64, "f32": LRR_PREC_F32, "mixed": LRR_PREC_MIXED}
 
 # every symbol include/dfc_lrr.h declares
-EXPORTS = ("lrr_workspace_bytes", "lrr_solve", "dfc_lrr_solve", "lrr_svt", "lrr_default_options", "lrr_status_string")
+EXPORTS = ("lrr_workspace_bytes", "lrr_solve", "dfc_lrr_solve", "lrr_svt", "lrr_gemm_bf16", "lrr_default_options",
+           "lrr_status_string")
 
 
 class LrrProblem(ctypes.Structure):
@@ -74,6 +75,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lrr_svt.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                             ctypes.c_void_p]
+    lib.lrr_gemm_bf16.restype = ctypes.c_int
+    lib.lrr_gemm_bf16.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                  ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
     lib.lrr_default_options.restype = None
     lib.lrr_default_options.argtypes = [ctypes.POINTER(LrrOptions)]
     lib.lrr_status_string.restype = ctypes.c_char_p
@@ -213,3 +217,19 @@ def svt(A, tau: float):
     if code < 0:
         raise LrrError(code)
     return J, int(rk.value)
+
+
+def gemm_bf16(A_km, B_km, M: int, N: int, K: int):
+    """C = A B on the tensor cores through the C ABI.  A_km: bf16 tensor of
+    shape (M, lda) holding A K-major (row m = A[m, :K]); B_km: bf16 tensor of
+    shape (N, ldb) holding B K-major (column n = B_km[n, :K]).  Returns C as a
+    float32 (M, N) tensor with column-major storage."""
+    import torch
+    lib = load()
+    C = torch.empty((N, M), dtype=torch.float32, device=A_km.device).t()
+    code = lib.lrr_gemm_bf16(ctypes.c_void_p(A_km.data_ptr()), A_km.stride(0), ctypes.c_void_p(B_km.data_ptr()),
+                             B_km.stride(0), ctypes.c_void_p(C.data_ptr()), C.stride(1), M, N, K,
+                             ctypes.c_void_p(torch.cuda.current_stream(A_km.device).cuda_stream))
+    if code < 0:
+        raise LrrError(code)
+    return C

@@ -11,15 +11,15 @@ __device__ __forceinline__ int circle_item(int pos, int r, int N) {
     return pos == 0 ? 0 : 1 + ((pos - 1 + r) % (N - 1));
 }
 
-// Diagonalises S (B2 x B2, row stride B2+1) in place by classical Jacobi
+// Diagonalises S (B2 x B2, row stride LDS) in place by classical Jacobi
 // rotations (angle from tan(2 theta) = 2 s_pq / (s_qq - s_pp)), B2/2 disjoint
 // rotations per parallel step, accumulating the rotations into R (R <- R J, R
 // must hold the identity on entry).  An entry is rotated while
 // |s_pq| > eps * sqrt(|s_pp s_qq|) and |s_pq| > floor_rot; sweeps stop after one
 // in which no entry above floor_sig was rotated, or after max_sweeps.
 // Returns nonzero (block-uniform) if any rotation was applied.
-template <typename T, int B2, int NT>
-__device__ int inner_jacobi(T (*S)[B2 + 1], T (*R)[B2 + 1], T* cs, T* sn, int* pi, int* qi, T floor_rot,
+template <typename T, int B2, int NT, int LDS = B2 + 1>
+__device__ int inner_jacobi(T (*S)[LDS], T (*R)[LDS], T* cs, T* sn, int* pi, int* qi, T floor_rot,
                             T floor_sig, int max_sweeps) {
     constexpr int b = B2 / 2;
     const int t = threadIdx.x;

@@ -28,11 +28,34 @@ constexpr bool kGramF64 = false;
 
 __device__ __forceinline__ int pcol(int i, int a, int c, int b) { return i < b ? a * b + i : c * b + (i - b); }
 
+// 16-byte vector of TI = 16 / sizeof(T) elements (float4 / double2)
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+
+__device__ __forceinline__ void unpack(const float4& v, float (&x)[4]) { x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w; }
+__device__ __forceinline__ void unpack(const double2& v, double (&x)[2]) { x[0] = v.x; x[1] = v.y; }
+
+// Copies rows r0 .. r0+B2-1 of the pivot columns of a column-major matrix into
+// a B2 x LD row-major shared tile (zero outside); consecutive threads read
+// consecutive rows of a column.
+template <typename T, int B2, int LD>
+__device__ __forceinline__ void load_chunk(T* tile, const T* __restrict__ base, int64_t ld, int rows, int ncol, int r0,
+                                           int a, int c, int b) {
+    for (int e = threadIdx.x; e < B2 * B2; e += NT) {
+        const int rr = e % B2, cc = e / B2;
+        const int gr = r0 + rr, gc = pcol(cc, a, c, b);
+        tile[rr * LD + cc] = (gr < rows && gc < ncol) ? base[gr + (int64_t)gc * ld] : T(0);
+    }
+}
+
 template <typename T, int B2>
 __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ descs, int round) {
     constexpr int b = B2 / 2;
     constexpr int TI = B2 / 16;        // each thread owns a TI x TI tile of the B2 x B2 products
-    constexpr int LD = B2 + 4;         // padded row stride of the shared tiles
+    constexpr int LD = B2 + 4;         // padded row stride of the shared tiles (16-byte rows)
+    using V = typename Vec16<T>::type;
+    static_assert(sizeof(V) == TI * sizeof(T), "tile width must match the 16-byte vector");
     const OsjDesc<T> d = descs[blockIdx.y];
     if (d.active && *d.active == 0) return;
     if (*d.done) return;
@@ -42,9 +65,10 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
     const int a = circle_item(P, round, nb), c = circle_item(nb - 1 - P, round, nb);
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* Xs = reinterpret_cast<T*>(smem_raw);          // B2 rows x LD
-    T(*S)[B2 + 1] = reinterpret_cast<T(*)[B2 + 1]>(Xs + B2 * LD);
-    T(*R)[B2 + 1] = S + B2;
+    T* const X0 = reinterpret_cast<T*>(smem_raw);   // one B2 x LD chunk tile
+    auto Xb = [&](int) { return X0; };
+    T(*S)[LD] = reinterpret_cast<T(*)[LD]>(X0 + B2 * LD);
+    T(*R)[LD] = S + B2;
     __shared__ T cs[b], sn[b];
     __shared__ int pi[b], qi[b];
     __shared__ T red[NT / 32];
@@ -56,19 +80,18 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
     const T floor2 = noise * noise * (*d.scale) + num<T>::tiny();
 
     // 1. pivot Gram S = X_P^T X_P from the columns of X, in B2-row chunks
+    //    (next chunk in flight while the current one is multiplied)
     using Acc = typename std::conditional<kGramF64, double, T>::type;
     Acc acc[TI][TI];
 #pragma unroll
     for (int u = 0; u < TI; ++u)
 #pragma unroll
         for (int v = 0; v < TI; ++v) acc[u][v] = Acc(0);
-    for (int r0 = 0; r0 < d.L; r0 += B2) {
-        for (int e = t; e < B2 * B2; e += NT) {
-            const int rr = e % B2, cc = e / B2;
-            const int gr = r0 + rr, gc = pcol(cc, a, c, b);
-            Xs[rr * LD + cc] = (gr < d.L && gc < d.p) ? d.X[gr + (int64_t)gc * d.ldx] : T(0);
-        }
+    const int nchunk = (d.L + B2 - 1) / B2;
+    for (int ch = 0; ch < nchunk; ++ch) {
+        load_chunk<T, B2, LD>(Xb(ch), d.X, d.ldx, d.L, d.p, ch * B2, a, c, b);
         __syncthreads();
+        const T* Xs = Xb(ch);
         T part[TI][TI];
 #pragma unroll
         for (int u = 0; u < TI; ++u)
@@ -77,8 +100,8 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
 #pragma unroll 4
         for (int rr = 0; rr < B2; ++rr) {
             T xi[TI], xj[TI];
-#pragma unroll
-            for (int u = 0; u < TI; ++u) { xi[u] = Xs[rr * LD + ti * TI + u]; xj[u] = Xs[rr * LD + tj * TI + u]; }
+            unpack(*reinterpret_cast<const V*>(Xs + rr * LD + ti * TI), xi);
+            unpack(*reinterpret_cast<const V*>(Xs + rr * LD + tj * TI), xj);
 #pragma unroll
             for (int u = 0; u < TI; ++u)
 #pragma unroll
@@ -142,7 +165,7 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
 
     // 3. rotate the pivot Gram to diagonal form; rotations that only mix noise
     //    columns (|s_pq| below floor2) do not keep the inner sweeps going
-    const int rot = inner_jacobi<T, B2, NT>(S, R, cs, sn, pi, qi, num<T>::tiny(), floor2, 4);
+    const int rot = inner_jacobi<T, B2, NT, LD>(S, R, cs, sn, pi, qi, num<T>::tiny(), floor2, 4);
     if (!rot) return;
 
     // R is a product of some thousand plane rotations, orthogonal only to
@@ -165,7 +188,8 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
 #pragma unroll
                 for (int v = 0; v < TI; ++v) g[u][v] = fma(ri[u], rj[v], g[u][v]);
         }
-        // Xs (free here) holds R^T R
+        // the first chunk buffer (free here) holds R^T R
+        T* Xs = Xb(0);
 #pragma unroll
         for (int u = 0; u < TI; ++u)
 #pragma unroll
@@ -196,18 +220,17 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
         __syncthreads();
     }
 
-    // 4. X_P <- X_P R and W_P <- W_P R, row chunk by row chunk
+    // 4. X_P <- X_P R and W_P <- W_P R, row chunk by row chunk (double-buffered)
     for (int pass = 0; pass < 2; ++pass) {
         T* base = pass == 0 ? d.X : d.W;
         const int64_t ld = pass == 0 ? d.ldx : d.ldw;
         const int rows = pass == 0 ? d.L : d.p;
-        for (int r0 = 0; r0 < rows; r0 += B2) {
-            for (int e = t; e < B2 * B2; e += NT) {
-                const int rr = e % B2, cc = e / B2;
-                const int gr = r0 + rr, gc = pcol(cc, a, c, b);
-                Xs[rr * LD + cc] = (gr < rows && gc < d.p) ? base[gr + (int64_t)gc * ld] : T(0);
-            }
+        const int nch = (rows + B2 - 1) / B2;
+        for (int ch = 0; ch < nch; ++ch) {
+            load_chunk<T, B2, LD>(Xb(ch), base, ld, rows, d.p, ch * B2, a, c, b);
             __syncthreads();
+            const T* Xs = Xb(ch);
+            const int r0 = ch * B2;
             T out[TI][TI];
 #pragma unroll
             for (int u = 0; u < TI; ++u)
@@ -215,9 +238,11 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
                 for (int v = 0; v < TI; ++v) out[u][v] = T(0);
 #pragma unroll 4
             for (int k = 0; k < B2; ++k) {
-                T xr[TI], rk[TI];
+                T xr[TI];
 #pragma unroll
-                for (int u = 0; u < TI; ++u) { xr[u] = Xs[(ti + 16 * u) * LD + k]; rk[u] = R[k][tj * TI + u]; }
+                for (int u = 0; u < TI; ++u) xr[u] = Xs[(ti + 16 * u) * LD + k];
+                T rk[TI];
+                unpack(*reinterpret_cast<const V*>(&R[k][tj * TI]), rk);
 #pragma unroll
                 for (int u = 0; u < TI; ++u)
 #pragma unroll
@@ -268,7 +293,7 @@ cudaError_t osj_sweeps(const OsjDesc<T>* d_desc, int nmat, int max_pp, int sweep
     constexpr int B2 = 2 * b;
     if (nmat <= 0 || max_pp <= 0) return cudaSuccess;
     const int nb = max_pp / b, npairs = nb / 2;
-    const size_t smem = sizeof(T) * (B2 * (B2 + 4) + 2 * B2 * (B2 + 1));
+    const size_t smem = sizeof(T) * 3 * B2 * (B2 + 4);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(osj_round<T, B2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -10,6 +10,8 @@
 //   M Z   =   U diag(sigma) Zt
 // E, Y1 and the residual C - M Z - E stay in the m-dimensional data space.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -75,12 +77,18 @@ __global__ void init_padded(T* __restrict__ G, int p, int pp, T diag, int eye) {
 // The Z-step kernel of the same iteration then accumulates the next value.
 template <typename T>
 __global__ void svt_gate(const int* __restrict__ act, double* __restrict__ afro, const double* __restrict__ mu,
-                         int* __restrict__ svt_on, T* __restrict__ scale, int* __restrict__ calls, int nblk) {
+                         int* __restrict__ svt_on, T* __restrict__ scale, int* __restrict__ calls,
+                         int* __restrict__ fp32_on, int* __restrict__ gemm32, double margin, int nblk) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nblk) return;
     const double tau = 1.0 / mu[b];
     svt_on[b] = (act[b] && afro[b] > tau * tau) ? 1 : 0;
     if (svt_on[b]) calls[b] += 1;
+    // mixed precision: float32 products from the first iteration in which
+    // ||A||_F exceeds margin * tau (sticky); before that J = 0 and the bf16
+    // rounding of the products is forgotten by the iteration
+    if (afro[b] > margin * margin * tau * tau) fp32_on[b] = 1;
+    gemm32[b] = (act[b] && fp32_on[b]) ? 1 : 0;
     if (act[b]) {
         scale[b] = (T)afro[b];
         afro[b] = 0.0;
@@ -161,7 +169,8 @@ __global__ void z_update(int r, int64_t n, const int* __restrict__ colblk, const
                          const double* __restrict__ mu, double rho, double mu_max, const T* __restrict__ Tt,
                          const T* __restrict__ Jt, T* __restrict__ Y2t, T* __restrict__ Zt, T* __restrict__ D,
                          T* __restrict__ A, const T* __restrict__ sig, const T* __restrict__ dinv,
-                         T* __restrict__ dmax, double* __restrict__ afro) {
+                         T* __restrict__ dmax, double* __restrict__ afro, uint16_t* __restrict__ zbf,
+                         int64_t ldz) {
     const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= n) return;
@@ -179,6 +188,7 @@ __global__ void z_update(int r, int64_t n, const int* __restrict__ colblk, const
         const T y2n = y2 + muT * dd;
         const T av = z + y2n * imun;
         Zt[o + i] = z;
+        if (zbf) zbf[i + j * ldz] = __bfloat16_as_ushort(__float2bfloat16((float)z));
         D[o + i] = dd;
         Y2t[o + i] = y2n;
         A[o + i] = av;
@@ -199,7 +209,7 @@ template <typename T>
 __global__ void e_update(int64_t m, int64_t n, const int* __restrict__ colblk, const int* __restrict__ act,
                          const double* __restrict__ mu, double rho, double mu_max, double lam,
                          const T* __restrict__ C, const T* __restrict__ MZ, T* __restrict__ Y1, T* __restrict__ E,
-                         T* __restrict__ P, T* __restrict__ r1max) {
+                         T* __restrict__ P, T* __restrict__ r1max, uint16_t* __restrict__ pbf, int64_t ldp) {
     const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= n) return;
@@ -226,7 +236,9 @@ __global__ void e_update(int64_t m, int64_t n, const int* __restrict__ colblk, c
         const T y1n = y1 + muT * l1;
         E[o + i] = e;
         Y1[o + i] = y1n;
-        P[o + i] = c - e + y1n * imun;
+        const T pv = c - e + y1n * imun;
+        P[o + i] = pv;
+        if (pbf) pbf[i + j * ldp] = __bfloat16_as_ushort(__float2bfloat16((float)pv));
         amax = fmax(amax, fabs(l1));
     }
     amax = warp_max(amax);
@@ -296,6 +308,27 @@ __global__ void setup_factors(const double* __restrict__ W, int64_t ldw, int64_t
         Ud[i + k * m] = u;
         Usd[i + k * m] = u / s;
     }
+}
+
+// bf16 copy of a column-major rows x cols matrix, same orientation, leading
+// dimension ldo (padding rows untouched): the K-major operand layout when the
+// contraction runs over the rows
+template <typename T>
+__global__ void to_bf16_km(const T* __restrict__ src, int64_t ld, int64_t rows, int64_t cols,
+                           uint16_t* __restrict__ dst, int64_t ldo) {
+    for (int64_t j = blockIdx.y; j < cols; j += gridDim.y)
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x)
+            dst[i + j * ldo] = __bfloat16_as_ushort(__float2bfloat16((float)src[i + j * ld]));
+}
+
+// bf16 transpose of a column-major rows x cols matrix: dst[j + i * ldo] = src(i, j)
+// (the K-major operand layout when the contraction runs over the columns)
+template <typename T>
+__global__ void to_bf16_transposed(const T* __restrict__ src, int64_t ld, int64_t rows, int64_t cols,
+                                   uint16_t* __restrict__ dst, int64_t ldo) {
+    for (int64_t i = blockIdx.y; i < rows; i += gridDim.y)
+        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols; j += (int64_t)gridDim.x * blockDim.x)
+            dst[j + i * ldo] = __bfloat16_as_ushort(__float2bfloat16((float)src[i + j * ld]));
 }
 
 template <typename T>

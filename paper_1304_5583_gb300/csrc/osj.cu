@@ -67,8 +67,13 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* const X0 = reinterpret_cast<T*>(smem_raw);   // one B2 x LD chunk tile
     auto Xb = [&](int) { return X0; };
-    T(*S)[LD] = reinterpret_cast<T(*)[LD]>(X0 + B2 * LD);
-    T(*R)[LD] = S + B2;
+    // S and R use an odd row stride (conflict-free for the inner Jacobi's
+    // scattered row/column pairs); after the rotation is final it is copied
+    // into R4 (stride LD, 16-byte rows, over S's space) for vector reads
+    constexpr int LO = B2 + 1;
+    T(*S)[LO] = reinterpret_cast<T(*)[LO]>(X0 + B2 * LD);
+    T(*R4)[LD] = reinterpret_cast<T(*)[LD]>(X0 + B2 * LD);
+    T(*R)[LO] = reinterpret_cast<T(*)[LO]>(X0 + 2 * B2 * LD);
     __shared__ T cs[b], sn[b];
     __shared__ int pi[b], qi[b];
     __shared__ T red[NT / 32];
@@ -165,7 +170,7 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
 
     // 3. rotate the pivot Gram to diagonal form; rotations that only mix noise
     //    columns (|s_pq| below floor2) do not keep the inner sweeps going
-    const int rot = inner_jacobi<T, B2, NT, LD>(S, R, cs, sn, pi, qi, num<T>::tiny(), floor2, 4);
+    const int rot = inner_jacobi<T, B2, NT, LO>(S, R, cs, sn, pi, qi, num<T>::tiny(), floor2, 4);
     if (!rot) return;
 
     // R is a product of some thousand plane rotations, orthogonal only to
@@ -220,6 +225,9 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
         __syncthreads();
     }
 
+    for (int e = t; e < B2 * B2; e += NT) R4[e / B2][e % B2] = R[e / B2][e % B2];
+    __syncthreads();
+
     // 4. X_P <- X_P R and W_P <- W_P R, row chunk by row chunk (double-buffered)
     for (int pass = 0; pass < 2; ++pass) {
         T* base = pass == 0 ? d.X : d.W;
@@ -227,7 +235,7 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
         const int rows = pass == 0 ? d.L : d.p;
         const int nch = (rows + B2 - 1) / B2;
         for (int ch = 0; ch < nch; ++ch) {
-            load_chunk<T, B2, LD>(Xb(ch), base, ld, rows, d.p, ch * B2, a, c, b);
+            load_chunk<T, B2, LO>(Xb(ch), base, ld, rows, d.p, ch * B2, a, c, b);
             __syncthreads();
             const T* Xs = Xb(ch);
             const int r0 = ch * B2;
@@ -240,9 +248,9 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
             for (int k = 0; k < B2; ++k) {
                 T xr[TI];
 #pragma unroll
-                for (int u = 0; u < TI; ++u) xr[u] = Xs[(ti + 16 * u) * LD + k];
+                for (int u = 0; u < TI; ++u) xr[u] = Xs[(ti + 16 * u) * LO + k];
                 T rk[TI];
-                unpack(*reinterpret_cast<const V*>(&R[k][tj * TI]), rk);
+                unpack(*reinterpret_cast<const V*>(&R4[k][tj * TI]), rk);
 #pragma unroll
                 for (int u = 0; u < TI; ++u)
 #pragma unroll
@@ -293,7 +301,7 @@ cudaError_t osj_sweeps(const OsjDesc<T>* d_desc, int nmat, int max_pp, int sweep
     constexpr int B2 = 2 * b;
     if (nmat <= 0 || max_pp <= 0) return cudaSuccess;
     const int nb = max_pp / b, npairs = nb / 2;
-    const size_t smem = sizeof(T) * 3 * B2 * (B2 + 4);
+    const size_t smem = sizeof(T) * (2 * B2 * (B2 + 4) + B2 * (B2 + 1));
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(osj_round<T, B2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -106,6 +106,10 @@ struct Buffers {
     T** Hp;
     T** T1p;
     int *pv, *ppv;
+    // mixed precision: bf16 K-major operands of the tensor-core products
+    int64_t ldm8, ldr8;
+    uint16_t *Ubf, *USbf, *Pbf, *Zbf;
+    int *fp32_on, *gemm32, *tc_err;
     // C step
     int *kept, *kept_n;
     double *Fd, *Gk, *Yd;
@@ -113,7 +117,7 @@ struct Buffers {
 };
 
 template <typename T>
-Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector<BlockInfo<T>>& blk) {
+Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector<BlockInfo<T>>& blk, bool mixed) {
     Buffers<T> b{};
     b.m = p->m;
     b.n = p->n;
@@ -206,6 +210,15 @@ Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector
     b.Yd = a.take<double>(r * p0);
     b.Q = a.take<T>(r * p0);
     b.Wc = a.take<T>(p0 * n);
+    b.ldm8 = (m + 7) / 8 * 8;
+    b.ldr8 = (r + 7) / 8 * 8;
+    b.Ubf = mixed ? a.take<uint16_t>(r * b.ldm8) : nullptr;
+    b.USbf = mixed ? a.take<uint16_t>(m * b.ldr8) : nullptr;
+    b.Pbf = mixed ? a.take<uint16_t>(n * b.ldm8) : nullptr;
+    b.Zbf = mixed ? a.take<uint16_t>(n * b.ldr8) : nullptr;
+    b.fp32_on = a.take<int>(t);
+    b.gemm32 = a.take<int>(t);
+    b.tc_err = a.take<int>(1);
     return b;
 }
 
@@ -295,7 +308,8 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     const auto blk = block_info<T>(p);
     const bool need_md = !std::is_same<Tin, double>::value;
     Arena probe(nullptr);
-    carve<T>(probe, p, need_md, blk);
+    const bool mixed = o->precision == LRR_PREC_MIXED;
+    carve<T>(probe, p, need_md, blk, mixed);
     const size_t need = probe.off + kAlign;
     void* own = nullptr;
     if (!ws) {
@@ -309,7 +323,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     } guard{own, s};
     if (ws_bytes < need - kAlign || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return LRR_ERR_WORKSPACE;
     Arena arena(ws);
-    Buffers<T> B = carve<T>(arena, p, need_md, blk);
+    Buffers<T> B = carve<T>(arena, p, need_md, blk, mixed);
     const int64_t m = p->m, n = p->n;
     const int t = p->t;
     const Tin* M = static_cast<const Tin*>(p->M);
@@ -391,6 +405,11 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     LRR_CUDA_TRY(cudaMemcpyAsync(B.lam, lam_sorted.data(), sizeof(double) * r, cudaMemcpyHostToDevice, s));
     k::setup_factors<<<dim3(grid1(m), (unsigned)r), 256, 0, s>>>(B.Wd, B.mpp, m, r, B.order, B.lam, B.Ud, B.Usd);
     k::setup_scalars<T><<<dim3(grid1(m), (unsigned)r), 256, 0, s>>>(B.lam, r, B.Ud, m, B.sig, B.dinv, B.U, B.US);
+    if (mixed) {
+        k::to_bf16_km<T><<<dim3(grid1(B.ldm8), (unsigned)r), 256, 0, s>>>(B.U, m, m, r, B.Ubf, B.ldm8);
+        k::to_bf16_transposed<T><<<dim3(grid1(B.ldr8), (unsigned)std::min<int64_t>(m, 65535)), 256, 0, s>>>(
+            B.US, m, m, r, B.USbf, B.ldr8);
+    }
     hd[1] = gdesc<double>(Md, ldmd, B.Usd, m, B.Vd, n, (int)n, r, (int)m, nullptr);
     LRR_CUDA_TRY(cudaMemcpyAsync(dd + 1, &hd[1], sizeof(GemmDesc<double>), cudaMemcpyHostToDevice, s));
     LRR_CUDA_TRY(gemm_grouped<double>(dd + 1, 1, true, false, (int)n, r, s));
@@ -473,8 +492,8 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         }
         orth1.push_back(gdesc<T>(B.W[i], pp_, B.W[i], pp_, B.T1[i], pp_, pi, pi, pi, B.svt_on + i));
         orth2.push_back(gdesc<T>(B.W[i], pp_, B.T1[i], pp_, B.H[i], pp_, pi, pi, pi, B.svt_on + i));
-        tmul.push_back(gdesc<T>(B.U, m, B.P + c0 * m, m, B.Tt + c0 * r, r, r, l, (int)m, B.act + i));
-        mzmul.push_back(gdesc<T>(B.US, m, B.Zt + c0 * r, r, B.MZ + c0 * m, m, (int)m, l, r, B.act + i));
+        tmul.push_back(gdesc<T>(B.U, m, B.P + c0 * m, m, B.Tt + c0 * r, r, r, l, (int)m, B.gemm32 + i));
+        mzmul.push_back(gdesc<T>(B.US, m, B.Zt + c0 * r, r, B.MZ + c0 * m, m, (int)m, l, r, B.gemm32 + i));
         GemmDesc<T> ex = gdesc<T>(B.V, n, B.D + c0 * r, r, nullptr, 0, (int)n, l, r, B.need_exact + i);
         ex.absmax = B.r2x + i;
         exact.push_back(ex);
@@ -509,6 +528,18 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     for (int i = 0; i < t; ++i)
         k::init_padded<T><<<grid1((int64_t)ppv[i] * ppv[i]), 256, 0, s>>>(B.W[i], pv[i], ppv[i], T(1), 1);
     LRR_CUDA_TRY(cudaMemsetAsync(B.afro, 0, sizeof(double) * t, s));
+    {
+        // mixed: every block starts on the bf16 tensor-core products (fp32_on = 0)
+        std::vector<int> f32init((size_t)t, mixed ? 0 : 1);
+        LRR_CUDA_TRY(cudaMemcpyAsync(B.fp32_on, f32init.data(), sizeof(int) * t, cudaMemcpyHostToDevice, s));
+        LRR_CUDA_TRY(cudaMemsetAsync(B.tc_err, 0, sizeof(int), s));
+        if (mixed) {
+            LRR_CUDA_TRY(cudaMemsetAsync(B.Pbf, 0, sizeof(uint16_t) * n * B.ldm8, s));
+            LRR_CUDA_TRY(cudaMemsetAsync(B.Zbf, 0, sizeof(uint16_t) * n * B.ldr8, s));
+            k::to_bf16_km<T><<<dim3(grid1(B.ldm8), (unsigned)std::min<int64_t>(n, 65535)), 256, 0, s>>>(
+                B.C, m, m, n, B.Pbf, B.ldm8);
+        }
+    }
     for (int i = 0; i < t; ++i)   // the SVT reconstruction reads it with zero weights before the first SVD
         LRR_CUDA_TRY(cudaMemsetAsync(B.T1[i], 0, sizeof(T) * (size_t)ppv[i] * ppv[i], s));
     LRR_CUDA_TRY(cudaMemsetAsync(B.jsweeps, 0, sizeof(int) * t, s));
@@ -525,6 +556,10 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     LRR_CUDA_TRY(cudaMemsetAsync(B.resid, 0, sizeof(double) * 2 * t, s));
 
     const int sweeps = o->jacobi_sweeps > 0 ? o->jacobi_sweeps : 12;
+    // mixed: a block leaves the bf16 products once ||A||_F > margin * tau, i.e.
+    // just before its SVT starts to act (J = 0 up to then)
+    const double switch_margin = mixed ? (o->mixed_switch > 0 ? o->mixed_switch : 0.5) : 0.0;
+    bool bf16_phase = mixed;
     const T jtol = sizeof(T) == 8 ? T(1e-13) : T(2e-6);
     const unsigned wgrid_n = (unsigned)((n * 32 + 255) / 256);
     const int nset = [&](int si) { return si < 0 ? 0 : 1; }(0);
@@ -535,7 +570,8 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         prof.iterations += 1;
         // J-step: SVT of A = Zt + Y2t/mu through the Gram eigendecomposition
         prof.begin();
-        k::svt_gate<T><<<ceil_div(t, 128), 128, 0, s>>>(B.act, B.afro, B.mu, B.svt_on, B.jscale, B.svtcalls, t);
+        k::svt_gate<T><<<ceil_div(t, 128), 128, 0, s>>>(B.act, B.afro, B.mu, B.svt_on, B.jscale, B.svtcalls,
+                                                         B.fp32_on, B.gemm32, switch_margin, t);
         LRR_CUDA_TRY(run_set(S_XT));
         LRR_CUDA_TRY(run_set(S_XW));
         prof.end(LRR_PH_GRAM, 1 + nl(S_XT) + nl(S_XW));
@@ -553,19 +589,30 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         prof.end(LRR_PH_SVT_APPLY, 5);
         // Z-step
         prof.begin();
+        if constexpr (std::is_same<T, float>::value) {
+            if (bf16_phase) {
+                // all columns at once; blocks already in float32 are recomputed below
+                LRR_CUDA_TRY(tc_gemm_bf16(B.Ubf, B.ldm8, B.Pbf, B.ldm8, B.Tt, r, r, (int)n, (int)m, B.tc_err, s));
+            }
+        }
         LRR_CUDA_TRY(run_set(S_T));
-        prof.end(LRR_PH_ZGEMM, 1);
+        prof.end(LRR_PH_ZGEMM, bf16_phase ? 2 : 1);
         prof.begin();
         k::z_update<T><<<wgrid_n, 256, 0, s>>>(r, n, B.colblk, B.act, B.mu, o->rho, o->mu_max, B.Tt, B.Jt, B.Y2t,
-                                               B.Zt, B.D, B.A, B.sig, B.dinv, B.dmax, B.afro);
+                                               B.Zt, B.D, B.A, B.sig, B.dinv, B.dmax, B.afro,
+                                               bf16_phase ? B.Zbf : nullptr, B.ldr8);
         prof.end(LRR_PH_ZUPDATE, 1);
         // E-step, residuals, duals
         prof.begin();
+        if constexpr (std::is_same<T, float>::value) {
+            if (bf16_phase)
+                LRR_CUDA_TRY(tc_gemm_bf16(B.USbf, B.ldr8, B.Zbf, B.ldr8, B.MZ, m, (int)m, (int)n, r, B.tc_err, s));
+        }
         LRR_CUDA_TRY(run_set(S_MZ));
-        prof.end(LRR_PH_MZGEMM, 1);
+        prof.end(LRR_PH_MZGEMM, bf16_phase ? 2 : 1);
         prof.begin();
         k::e_update<T><<<wgrid_n, 256, 0, s>>>(m, n, B.colblk, B.act, B.mu, o->rho, o->mu_max, o->lambda, B.C,
-                                               B.MZ, B.Y1, B.E, B.P, B.r1);
+                                               B.MZ, B.Y1, B.E, B.P, B.r1, bf16_phase ? B.Pbf : nullptr, B.ldm8);
         prof.end(LRR_PH_EUPDATE, 1);
         prof.begin();
         k::stop_part1<T><<<ceil_div(t, 128), 128, 0, s>>>(t, B.act, B.r1, B.dmax, nu_h, 1.0 / std::sqrt((double)n), o->eps, B.need_exact,
@@ -581,7 +628,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     };
     auto run_loop = [&](const std::vector<int>& act0) -> int {
         LRR_CUDA_TRY(cudaMemcpyAsync(B.act, act0.data(), sizeof(int) * t, cudaMemcpyHostToDevice, s));
-        std::vector<int> ah((size_t)t);
+        std::vector<int> ah((size_t)t), fh((size_t)t);
         int done_it = 0;
         const int chunk = 4;
         while (done_it < o->max_iter) {
@@ -591,9 +638,15 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
             }
             prof.begin();
             LRR_CUDA_TRY(cudaMemcpyAsync(ah.data(), B.act, sizeof(int) * t, cudaMemcpyDeviceToHost, s));
+            if (bf16_phase) LRR_CUDA_TRY(cudaMemcpyAsync(fh.data(), B.fp32_on, sizeof(int) * t, cudaMemcpyDeviceToHost, s));
             prof.end(LRR_PH_HOST, 0);
             LRR_CUDA_TRY(cudaStreamSynchronize(s));
             prof.flush();
+            if (bf16_phase) {
+                bool any16 = false;
+                for (int i = 0; i < t; ++i) any16 |= (ah[i] != 0 && fh[i] == 0);
+                if (!any16) bf16_phase = false;
+            }
             if (std::none_of(ah.begin(), ah.end(), [](int v) { return v != 0; })) break;
         }
         return LRR_OK;
@@ -681,6 +734,8 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         prof.calls[LRR_PH_COMBINE] += cl;
     }
 
+    int tc_err_h = 0;
+    LRR_CUDA_TRY(cudaMemcpyAsync(&tc_err_h, B.tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     std::vector<int> iters_h((size_t)t), conv_h((size_t)t);
     std::vector<double> resid_h((size_t)2 * t);
     LRR_CUDA_TRY(cudaMemcpyAsync(iters_h.data(), B.iters, sizeof(int) * t, cudaMemcpyDeviceToHost, s));
@@ -720,6 +775,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
             res->timings_ms[0] = a; res->timings_ms[1] = b2; res->timings_ms[2] = c;
         }
     }
+    if (tc_err_h) return LRR_ERR_CUDA;   // a tensor-core product timed out
     for (int i = 0; i < t; ++i)
         if (!conv_h[i]) return LRR_NOT_CONVERGED;
     return LRR_OK;
@@ -821,10 +877,10 @@ int svt_impl(const T* A, int64_t rows, int64_t cols, int64_t lda, double tau, T*
 }
 
 template <typename T, typename Tin>
-size_t workspace_impl(const lrr_problem* p) {
+size_t workspace_impl(const lrr_problem* p, bool mixed) {
     const auto blk = block_info<T>(p);
     Arena probe(nullptr);
-    carve<T>(probe, p, !std::is_same<Tin, double>::value, blk);
+    carve<T>(probe, p, !std::is_same<Tin, double>::value, blk, mixed);
     return probe.off + kAlign;
 }
 
@@ -833,7 +889,8 @@ int dispatch(const lrr_problem* p, const lrr_options* o, void* ws, size_t wsb, l
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     switch (o->precision) {
         case LRR_PREC_F64: return solve_impl<double, double>(p, o, ws, wsb, r, s, dfc);
-        case LRR_PREC_F32: return solve_impl<float, float>(p, o, ws, wsb, r, s, dfc);
+        case LRR_PREC_F32:
+        case LRR_PREC_MIXED: return solve_impl<float, float>(p, o, ws, wsb, r, s, dfc);
         default: return LRR_ERR_UNSUPPORTED;
     }
 }
@@ -846,8 +903,9 @@ extern "C" {
 size_t lrr_workspace_bytes(const lrr_problem* p, const lrr_options* o) {
     if (!lrr::valid_problem(p, o)) return 0;
     switch (o->precision) {
-        case LRR_PREC_F64: return lrr::workspace_impl<double, double>(p);
-        case LRR_PREC_F32: return lrr::workspace_impl<float, float>(p);
+        case LRR_PREC_F64: return lrr::workspace_impl<double, double>(p, false);
+        case LRR_PREC_F32: return lrr::workspace_impl<float, float>(p, false);
+        case LRR_PREC_MIXED: return lrr::workspace_impl<float, float>(p, true);
         default: return 0;
     }
 }

@@ -112,9 +112,15 @@ class SolveResult:
 
 def column_major(x):
     """(rows, cols) tensor with unit row stride (a column-major matrix); copies if needed."""
-    if x.dim() == 2 and x.stride(0) == 1 and x.stride(1) >= max(1, x.shape[0]):
+    if x.dim() == 2 and x.stride(0) == 1 and (x.stride(1) >= max(1, x.shape[0]) or x.shape[1] == 1):
         return x
     return x.t().contiguous().t()
+
+
+def leading_dim(x):
+    """Leading dimension of a column-major (rows, cols) tensor (a single
+    column's stride is arbitrary in torch: use rows)."""
+    return x.stride(1) if x.shape[1] > 1 else max(1, x.shape[0])
 
 
 def options(lam: float, rho: float = 1.1, mu0: float = 1e-6, mu_max: float = 1e10, eps: float = 1e-6,
@@ -134,7 +140,7 @@ def _problem(M, perm, offsets):
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
     p = LrrProblem()
     p.M = ctypes.c_void_p(M.data_ptr())
-    p.m, p.n, p.ldm = M.shape[0], M.shape[1], M.stride(1)
+    p.m, p.n, p.ldm = M.shape[0], M.shape[1], leading_dim(M)
     p.t = len(offsets) - 1
     p.perm = perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
     p.offsets = offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
@@ -212,8 +218,8 @@ def svt(A, tau: float):
     J = torch.empty((cols, rows), dtype=A.dtype, device=A.device).t()
     prec = LRR_PREC_F64 if A.dtype == torch.float64 else LRR_PREC_F32
     rk = ctypes.c_int32(0)
-    code = lib.lrr_svt(ctypes.c_void_p(A.data_ptr()), rows, cols, A.stride(1), float(tau), ctypes.c_void_p(J.data_ptr()),
-                       J.stride(1), prec, ctypes.byref(rk), ctypes.c_void_p(torch.cuda.current_stream(A.device).cuda_stream))
+    code = lib.lrr_svt(ctypes.c_void_p(A.data_ptr()), rows, cols, leading_dim(A), float(tau),
+                       ctypes.c_void_p(J.data_ptr()), leading_dim(J), prec, ctypes.byref(rk), ctypes.c_void_p(torch.cuda.current_stream(A.device).cuda_stream))
     if code < 0:
         raise LrrError(code)
     return J, int(rk.value)

@@ -92,3 +92,79 @@ def test_invalid_partition_is_rejected(lib):
     bad[0] = bad[1]
     res = binding.dfc_lrr_solve(_to_dev(w.M, np.float32), bad, w.offsets, o, raise_on_error=False)
     assert res.status == -1
+
+
+def test_small_dfc_mixed_precision_matches_oracle(lib):
+    w = synth.workload("small_dfc_60x240")
+    res, M = _run(lib, w, "mixed")
+    assert res.status == 0
+    ref = olrr.dfc_lrr(M, w.perm, w.offsets, w.lam, eps=w.eps, max_iter=w.max_iter, fixed_iters=list(res.iters))
+    assert _rel(res.Z.cpu().numpy(), ref.Z) < 1e-5
+    assert _rel(res.S.cpu().numpy(), ref.S) < 1e-5
+
+
+@pytest.mark.parametrize("precision", ["f32", "mixed", "f64"])
+def test_tiny_and_ragged_shapes(lib, precision):
+    """m not a multiple of 8, blocks of one and two columns, t close to n."""
+    d = synth.union_of_subspaces(21, 13, 2, 2, 9, 0.1)
+    M = d.M
+    n = M.shape[1]
+    perm = np.random.default_rng(3).permutation(n)
+    offsets = np.array([0, 1, 3, 8, n], dtype=np.int64)
+    w = synth.Workload("ragged", d, perm, offsets, lam=0.3, eps=1e-6 if precision != "f64" else 1e-9)
+    res, Mr = _run(lib, w, precision)
+    assert res.status == 0
+    ref = olrr.dfc_lrr(Mr, perm, offsets, w.lam, eps=w.eps, fixed_iters=list(res.iters))
+    tol = 1e-9 if precision == "f64" else 1e-5
+    assert _rel(res.Z.cpu().numpy(), ref.Z) < tol
+    # S is mostly zero columns, so its relative error is the least forgiving;
+    # in the mixed form the bf16 warm-up phase leaves ~1e-5 there
+    assert _rel(res.S.cpu().numpy(), ref.S) < (1e-4 if precision == "mixed" else tol)
+
+
+def test_segmentation_labels_identical_plain_lrr(lib):
+    """Segmentation (Section 4.1.2 post-processing) of the GPU and oracle
+    estimates gives the same partition on the 100 x 500 problem."""
+    from oracle import segment
+    w = synth.workload("plain_lrr_100x500")
+    res, M = _run(lib, w, "f64", entry="lrr")
+    ref = olrr.dfc_lrr(M, w.perm, w.offsets, w.lam, eps=w.eps)
+    a = segment.segment(res.Z.cpu().numpy(), w.data.k, seed=0)
+    b = segment.segment(ref.Z, w.data.k, seed=0)
+    assert segment.same_partition(a, b)
+
+
+def test_zero_matrix_reports_rank_error(lib):
+    from paper_1304_5583_gb300 import binding
+    w = synth.workload("tiny_20x30")
+    res = binding.dfc_lrr_solve(_to_dev(np.zeros_like(w.M), np.float32), w.perm, w.offsets, binding.options(0.1),
+                                raise_on_error=False)
+    assert res.status == -5
+
+
+def _block0_projected(M, perm, offsets, lam, eps, it0):
+    fx = olrr.dfc_lrr(M, perm, offsets, lam, eps=eps, blocks_only=[0],
+                      fixed_iters=[int(it0)] + [0] * (len(offsets) - 2))
+    b0 = fx.blocks[0]
+    Q = olrr.orth_basis(b0.J_U)
+    return Q @ (Q.T @ b0.Z), Q.shape[1]
+
+
+@pytest.mark.parametrize("name,precision", [("dfc_500x5000", "f32"), ("dfc_faces_2016x2432", "mixed")])
+def test_full_size_block_one_matches_oracle(lib, name, precision):
+    """Full-size workloads, sampled: the C-step output on block 1's columns is
+    Q1 Q1^T Z_1, which the oracle computes from block 1 alone at the GPU's
+    iteration count for that block."""
+    w = synth.workload(name)
+    res, M = _run(lib, w, precision)
+    assert res.status == 0
+    assert np.all(res.resid.max(axis=1) < w.eps)
+    Zp, k1 = _block0_projected(M, w.perm, w.offsets, w.lam, w.eps, res.iters[0])
+    cols = w.perm[w.offsets[0]:w.offsets[1]]
+    # the SVT rank of block 1 counts singular values above tau; on data whose
+    # spectrum decays smoothly through tau (the face-like workload) directions
+    # within rounding of tau can fall either way, each carrying a weight of
+    # order its distance to tau, so the count is compared loosely and the
+    # projected values tightly
+    assert abs(res.k1 - k1) <= max(2, 0.1 * k1), (res.k1, k1)
+    assert _rel(res.Z.cpu().numpy()[:, cols], Zp) < 1e-5

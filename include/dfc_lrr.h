@@ -51,7 +51,8 @@ typedef enum {
     LRR_ERR_CUDA = -3,          /* a CUDA runtime call failed                        */
     LRR_ERR_WORKSPACE = -4,     /* workspace too small or misaligned                 */
     LRR_ERR_RANK = -5,          /* M is numerically zero                             */
-    LRR_ERR_UNSUPPORTED = -6    /* option combination not built (see lrr_status_string) */
+    LRR_ERR_UNSUPPORTED = -6,   /* option combination not built (see lrr_status_string) */
+    LRR_ERR_TOO_LARGE = -7      /* problem exceeds lrr_svt_noalloc's fixed scratch array */
 } lrr_status;
 
 typedef enum {
@@ -156,6 +157,29 @@ LRR_API int dfc_lrr_solve(const lrr_problem* p, const lrr_options* o, void* work
  * rows, cols <= 65536. */
 LRR_API int lrr_svt(const void* A, int64_t rows, int64_t cols, int64_t lda, double tau, void* J, int64_t ldj,
                     int32_t precision, int32_t* rank, void* stream);
+
+/* lrr_svt without any memory allocation.  Same operation, arguments and
+ * result as lrr_svt; the paper has no counterpart -- this entry point exists
+ * for callers that cannot allocate device memory while they call it: code
+ * running while a stream is being captured into a CUDA graph (an allocation
+ * would become part of the graph or fail), code whose device memory is owned
+ * by another allocator that must not be bypassed, and latency-bound loops
+ * where growing a memory pool could stall.
+ * Scratch: one file-scope device array of lrr_svt_noalloc_capacity() bytes
+ * (32 MiB), present on every device that loads the library until the process
+ * exits.  A problem whose scratch would exceed it (float32 square matrices up
+ * to about 1400 x 1400, float64 about 1000 x 1000) returns LRR_ERR_TOO_LARGE.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and must come before any stream capture.  Every call uses
+ * the same array and writes everything it reads, so calls are independent
+ * when they run one after another; calls that overlap on the GPU (several
+ * streams or host threads at once) race on the array and must not be issued.
+ * The call synchronises `stream`. */
+LRR_API int lrr_svt_noalloc(const void* A, int64_t rows, int64_t cols, int64_t lda, double tau, void* J, int64_t ldj,
+                            int32_t precision, int32_t* rank, void* stream);
+
+/* Size in bytes of lrr_svt_noalloc's fixed scratch array. */
+LRR_API size_t lrr_svt_noalloc_capacity(void);
 
 /* The tensor-core product of the mixed-precision iteration on its own:
  * C = A B with A (M x K) and B (K x N) bf16, both stored K-major (element

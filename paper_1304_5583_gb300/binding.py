@@ -21,8 +21,8 @@ LRR_PREC_F64, LRR_PREC_F32, LRR_PREC_MIXED = 0, 1, 2
 PRECISIONS = {"f64": LRR_PREC_F64, "f32": LRR_PREC_F32, "mixed": LRR_PREC_MIXED}
 
 # every symbol include/dfc_lrr.h declares
-EXPORTS = ("lrr_workspace_bytes", "lrr_solve", "dfc_lrr_solve", "lrr_svt", "lrr_gemm_bf16", "lrr_default_options",
-           "lrr_status_string")
+EXPORTS = ("lrr_workspace_bytes", "lrr_solve", "dfc_lrr_solve", "lrr_svt", "lrr_svt_noalloc",
+           "lrr_svt_noalloc_capacity", "lrr_gemm_bf16", "lrr_default_options", "lrr_status_string")
 
 
 class LrrProblem(ctypes.Structure):
@@ -75,6 +75,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lrr_svt.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                             ctypes.c_void_p]
+    lib.lrr_svt_noalloc.restype = ctypes.c_int
+    lib.lrr_svt_noalloc.argtypes = lib.lrr_svt.argtypes
+    lib.lrr_svt_noalloc_capacity.restype = ctypes.c_size_t
+    lib.lrr_svt_noalloc_capacity.argtypes = []
     lib.lrr_gemm_bf16.restype = ctypes.c_int
     lib.lrr_gemm_bf16.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                   ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
@@ -209,8 +213,9 @@ def lrr_solve(M, perm, opts: LrrOptions, **kw) -> SolveResult:
     return _solve("lrr_solve", M, perm, np.array([0, n], np.int64), opts, **kw)
 
 
-def svt(A, tau: float):
-    """Singular-value thresholding through the C ABI: returns (J, rank)."""
+def svt(A, tau: float, no_alloc: bool = False):
+    """Singular-value thresholding through the C ABI: returns (J, rank).
+    no_alloc=True calls lrr_svt_noalloc (fixed device scratch, no allocation)."""
     import torch
     lib = load()
     A = column_major(A)
@@ -218,7 +223,8 @@ def svt(A, tau: float):
     J = torch.empty((cols, rows), dtype=A.dtype, device=A.device).t()
     prec = LRR_PREC_F64 if A.dtype == torch.float64 else LRR_PREC_F32
     rk = ctypes.c_int32(0)
-    code = lib.lrr_svt(ctypes.c_void_p(A.data_ptr()), rows, cols, leading_dim(A), float(tau),
+    fn = lib.lrr_svt_noalloc if no_alloc else lib.lrr_svt
+    code = fn(ctypes.c_void_p(A.data_ptr()), rows, cols, leading_dim(A), float(tau),
                        ctypes.c_void_p(J.data_ptr()), leading_dim(J), prec, ctypes.byref(rk), ctypes.c_void_p(torch.cuda.current_stream(A.device).cuda_stream))
     if code < 0:
         raise LrrError(code)

@@ -19,6 +19,7 @@
 #include <cstring>
 #include <numeric>
 #include <type_traits>
+#include <mutex>
 #include <vector>
 
 #include "dfc_lrr.h"
@@ -876,6 +877,127 @@ int svt_impl(const T* A, int64_t rows, int64_t cols, int64_t lda, double tau, T*
     return LRR_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// lrr_svt_noalloc: the stand-alone SVT with all of its scratch in one
+// file-scope device array instead of a stream-ordered allocation.
+//
+// Capacity: kNoAllocScratchBytes (32 MiB) on every device that loads this
+// library, held until the process exits.  The device address of the array is
+// looked up once per device (cudaGetSymbolAddress, with that device current)
+// by the first call made on it; make that first call before capturing the
+// stream into a CUDA graph.  All calls share the array: every value a call
+// reads is written by the same call first, and calls whose work overlaps on
+// the GPU (two streams, two host threads) race on it.
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
+static __device__ __align__(256) unsigned char g_svt_scratch[kNoAllocScratchBytes];
+
+std::mutex g_scratch_mutex;
+void* g_scratch_ptr[64] = {};
+
+// device address of g_svt_scratch on the current device (nullptr on failure)
+void* svt_scratch_address() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_svt_scratch) != cudaSuccess) return nullptr;
+        g_scratch_ptr[dev] = p;
+    }
+    return g_scratch_ptr[dev];
+}
+
+template <typename T>
+int svt_noalloc_impl(const T* A, int64_t rows, int64_t cols, int64_t lda, double tau, T* J, int64_t ldj,
+                     int32_t* rank_out, cudaStream_t s) {
+    constexpr int B2 = 2 * jacobi_bs<T>();
+    const bool tall = cols <= rows;
+    const int p = (int)std::min(rows, cols);
+    const int L = (int)(tall ? rows : cols);
+    const int pp = round_up(p, B2);
+    struct Parts {
+        T *X, *W, *H, *T1, *h, *scl, *off;
+        T **Wp, **Hp, **hp, **T1p;
+        int* ints;
+        double* dbl;
+        OsjDesc<T>* od;
+        GemmDesc<T>* gd;
+    };
+    auto lay = [&](Arena& a) {
+        Parts q;
+        q.X = a.take<T>((size_t)L * p);
+        q.W = a.take<T>((size_t)pp * pp);
+        q.H = a.take<T>((size_t)pp * pp);
+        q.T1 = a.take<T>((size_t)pp * pp);
+        q.h = a.take<T>(pp);
+        q.ints = a.take<int>(16);
+        q.dbl = a.take<double>(4);
+        q.od = a.take<OsjDesc<T>>(1);
+        q.gd = a.take<GemmDesc<T>>(8);
+        q.Wp = a.take<T*>(1);
+        q.Hp = a.take<T*>(1);
+        q.hp = a.take<T*>(1);
+        q.T1p = a.take<T*>(1);
+        q.scl = a.take<T>(1);
+        q.off = a.take<T>(1);
+        return q;
+    };
+    Arena sz(nullptr);
+    lay(sz);
+    if (sz.off > kNoAllocScratchBytes) return LRR_ERR_TOO_LARGE;
+    void* base = svt_scratch_address();
+    if (!base) return LRR_ERR_CUDA;
+    Arena a(base);
+    const Parts q = lay(a);
+    int* act = q.ints;
+    int* on = q.ints + 1;
+    int* rk = q.ints + 2;
+    int* done = q.ints + 3;
+    int* swp = q.ints + 4;
+    int* pv = q.ints + 8;
+    int* ppv = q.ints + 9;
+    double* mu = q.dbl;
+    const int one[2] = {1, 1};
+    const double mud = 1.0 / tau;
+    const int pvals[2] = {p, pp};
+    T* ptrs[4] = {q.W, q.H, q.h, q.T1};
+    LRR_CUDA_TRY(cudaMemcpyAsync(act, one, sizeof(int) * 2, cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemsetAsync(swp, 0, sizeof(int), s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(mu, &mud, sizeof(double), cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(pv, pvals, sizeof(int) * 2, cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(q.Wp, &ptrs[0], sizeof(T*), cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(q.Hp, &ptrs[1], sizeof(T*), cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(q.hp, &ptrs[2], sizeof(T*), cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(q.T1p, &ptrs[3], sizeof(T*), cudaMemcpyHostToDevice, s));
+    k::init_padded<T><<<grid1((int64_t)pp * pp), 256, 0, s>>>(q.W, p, pp, T(1), 1);
+    OsjDesc<T> d{};
+    d.X = q.X; d.W = q.W; d.done = done; d.off = q.off; d.active = on; d.scale = q.scl; d.mu = mu;
+    d.ldx = L; d.ldw = pp; d.L = L; d.p = p; d.pp = pp; d.strict = 1;
+    LRR_CUDA_TRY(cudaMemcpyAsync(q.od, &d, sizeof(d), cudaMemcpyHostToDevice, s));
+    GemmDesc<T> g[4];
+    g[0] = gdesc<T>(A, lda, q.W, pp, q.X, L, L, p, p, nullptr);                         // X = A W or A^T W
+    g[1] = gdesc<T>(q.W, pp, q.W, pp, q.T1, pp, p, p, p, nullptr);                      // W^T W
+    g[2] = gdesc<T>(q.W, pp, q.T1, pp, q.H, pp, p, p, p, nullptr);                      // W (W^T W)
+    if (tall) g[3] = gdesc<T>(q.X, L, q.T1, pp, J, ldj, (int)rows, (int)cols, p, nullptr);
+    else g[3] = gdesc<T>(q.T1, pp, q.X, L, J, ldj, (int)rows, (int)cols, p, nullptr);
+    g[3].kscale = q.h;
+    LRR_CUDA_TRY(cudaMemcpyAsync(q.gd, g, sizeof(g), cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(gemm_grouped<T>(q.gd, 1, !tall, false, L, p, s));
+    k::col_norm_max<T><<<1, 256, 0, s>>>(q.od, on, q.scl, 1);
+    LRR_CUDA_TRY(osj_sweeps<T>(q.od, 1, pp, 40, sizeof(T) == 8 ? T(1e-13) : T(2e-6), swp, s));
+    k::svt_weights<T><<<1, 256, 0, s>>>(q.od, q.hp, act, on, mu, rk, 1);
+    LRR_CUDA_TRY(gemm_grouped<T>(q.gd + 1, 1, true, false, p, p, s));
+    LRR_CUDA_TRY(gemm_grouped<T>(q.gd + 2, 1, false, false, p, p, s));
+    k::ns_orth<T><<<dim3(64, 1), 256, 0, s>>>(q.Wp, q.Hp, q.T1p, pv, ppv, on, 1);
+    LRR_CUDA_TRY(gemm_grouped<T>(q.gd + 3, 1, false, true, (int)rows, (int)cols, s));
+    int rk_h = 0;
+    LRR_CUDA_TRY(cudaMemcpyAsync(&rk_h, rk, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LRR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (rank_out) *rank_out = rk_h;
+    return LRR_OK;
+}
+
 template <typename T, typename Tin>
 size_t workspace_impl(const lrr_problem* p, bool mixed) {
     const auto blk = block_info<T>(p);
@@ -952,6 +1074,22 @@ int lrr_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float*
     return rc;
 }
 
+int lrr_svt_noalloc(const void* A, int64_t rows, int64_t cols, int64_t lda, double tau, void* J, int64_t ldj,
+                    int32_t precision, int32_t* rank, void* stream) {
+    if (!A || !J || rows < 1 || cols < 1 || lda < rows || ldj < rows || !(tau > 0)) return LRR_ERR_INVALID;
+    if (rows > (1 << 16) || cols > (1 << 16)) return LRR_ERR_TOO_LARGE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == LRR_PREC_F64)
+        return lrr::svt_noalloc_impl<double>(static_cast<const double*>(A), rows, cols, lda, tau,
+                                             static_cast<double*>(J), ldj, rank, s);
+    if (precision == LRR_PREC_F32)
+        return lrr::svt_noalloc_impl<float>(static_cast<const float*>(A), rows, cols, lda, tau, static_cast<float*>(J),
+                                            ldj, rank, s);
+    return LRR_ERR_UNSUPPORTED;
+}
+
+size_t lrr_svt_noalloc_capacity(void) { return lrr::kNoAllocScratchBytes; }
+
 void lrr_default_options(lrr_options* o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
@@ -978,6 +1116,7 @@ const char* lrr_status_string(int s) {
         case LRR_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
         case LRR_ERR_RANK: return "M is numerically zero";
         case LRR_ERR_UNSUPPORTED: return "precision mode not available";
+        case LRR_ERR_TOO_LARGE: return "problem does not fit the fixed scratch array of lrr_svt_noalloc";
         default: return "unknown status";
     }
 }

@@ -285,7 +285,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dfc_1000x20000")
-    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["f32", "f64", "mixed"])
     ap.add_argument("--sequential", action="store_true", help="solve the blocks one at a time")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=1)

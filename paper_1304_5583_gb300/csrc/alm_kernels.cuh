@@ -163,14 +163,16 @@ __global__ void svt_weights(const OsjDesc<T>* __restrict__ descs, T* const* __re
 }
 
 // Z-step in reduced coordinates, fused with the Y2 dual step and the next
-// SVT input; one warp per column.
+// SVT input; one warp per column.  With T = U^T (Y1/mu - E) on entry:
+//   Zt = (sigma (Theta + T) + Jt - Y2t/mu) / (1 + sigma^2)
+//   T <- Delta = Theta - sigma Zt   (so that C - M Z = C_perp + U Delta)
 template <typename T>
 __global__ void z_update(int r, int64_t n, const int* __restrict__ colblk, const int* __restrict__ act,
-                         const double* __restrict__ mu, double rho, double mu_max, const T* __restrict__ Tt,
-                         const T* __restrict__ Jt, T* __restrict__ Y2t, T* __restrict__ Zt, T* __restrict__ D,
-                         T* __restrict__ A, const T* __restrict__ sig, const T* __restrict__ dinv,
-                         T* __restrict__ dmax, double* __restrict__ afro, uint16_t* __restrict__ zbf,
-                         int64_t ldz) {
+                         const double* __restrict__ mu, double rho, double mu_max, T* __restrict__ Tt,
+                         const T* __restrict__ Theta, const T* __restrict__ Jt, T* __restrict__ Y2t,
+                         T* __restrict__ Zt, T* __restrict__ D, T* __restrict__ A, const T* __restrict__ sig,
+                         const T* __restrict__ dinv, T* __restrict__ dmax, double* __restrict__ afro,
+                         uint16_t* __restrict__ dbf, int64_t ldd) {
     const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= n) return;
@@ -182,13 +184,15 @@ __global__ void z_update(int r, int64_t n, const int* __restrict__ colblk, const
     const int64_t o = j * r;
     T acc = T(0), aacc = T(0);
     for (int i = lane; i < r; i += 32) {
-        const T tv = Tt[o + i], jv = Jt[o + i], y2 = Y2t[o + i];
-        const T z = dinv[i] * (sig[i] * tv + jv - y2 * imu);
+        const T th = Theta[o + i], jv = Jt[o + i], y2 = Y2t[o + i];
+        const T z = dinv[i] * (sig[i] * (th + Tt[o + i]) + jv - y2 * imu);
+        const T dl = th - sig[i] * z;
         const T dd = z - jv;
         const T y2n = y2 + muT * dd;
         const T av = z + y2n * imun;
         Zt[o + i] = z;
-        if (zbf) zbf[i + j * ldz] = __bfloat16_as_ushort(__float2bfloat16((float)z));
+        Tt[o + i] = dl;
+        if (dbf) dbf[i + j * ldd] = __bfloat16_as_ushort(__float2bfloat16((float)dl));
         D[o + i] = dd;
         Y2t[o + i] = y2n;
         A[o + i] = av;
@@ -204,12 +208,13 @@ __global__ void z_update(int r, int64_t n, const int* __restrict__ colblk, const
 }
 
 // E-step (column shrinkage), primal residual, Y1 dual step and the next
-// Z-step right-hand side P = C - E + Y1/mu'; one warp per column.
+// Z-step right-hand side Q = Y1/mu' - E; one warp per column.  The residual
+// C - M Z arrives as C_perp + U Delta (Cp may be null when C_perp = 0).
 template <typename T>
 __global__ void e_update(int64_t m, int64_t n, const int* __restrict__ colblk, const int* __restrict__ act,
                          const double* __restrict__ mu, double rho, double mu_max, double lam,
-                         const T* __restrict__ C, const T* __restrict__ MZ, T* __restrict__ Y1, T* __restrict__ E,
-                         T* __restrict__ P, T* __restrict__ r1max, uint16_t* __restrict__ pbf, int64_t ldp) {
+                         const T* __restrict__ Cp, const T* __restrict__ UD, T* __restrict__ Y1, T* __restrict__ E,
+                         T* __restrict__ Q, T* __restrict__ r1max, uint16_t* __restrict__ qbf, int64_t ldq) {
     const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= n) return;
@@ -222,23 +227,25 @@ __global__ void e_update(int64_t m, int64_t n, const int* __restrict__ colblk, c
     const int64_t o = j * m;
     T acc = T(0);
     for (int64_t i = lane; i < m; i += 32) {
-        const T x = C[o + i] - MZ[o + i] + Y1[o + i] * imu;
+        const T res = (Cp ? Cp[o + i] : T(0)) + UD[o + i];
+        const T x = res + Y1[o + i] * imu;
         acc += x * x;
     }
     const T nrm = sqrt(warp_sum(acc));
     const T sc = nrm > thr ? T(1) - thr / nrm : T(0);
     T amax = T(0);
     for (int64_t i = lane; i < m; i += 32) {
-        const T c = C[o + i], mz = MZ[o + i], y1 = Y1[o + i];
-        const T x = c - mz + y1 * imu;
+        const T res = (Cp ? Cp[o + i] : T(0)) + UD[o + i];
+        const T y1 = Y1[o + i];
+        const T x = res + y1 * imu;
         const T e = sc * x;
-        const T l1 = c - mz - e;
+        const T l1 = res - e;
         const T y1n = y1 + muT * l1;
         E[o + i] = e;
         Y1[o + i] = y1n;
-        const T pv = c - e + y1n * imun;
-        P[o + i] = pv;
-        if (pbf) pbf[i + j * ldp] = __bfloat16_as_ushort(__float2bfloat16((float)pv));
+        const T qv = y1n * imun - e;
+        Q[o + i] = qv;
+        if (qbf) qbf[i + j * ldq] = __bfloat16_as_ushort(__float2bfloat16((float)qv));
         amax = fmax(amax, fabs(l1));
     }
     amax = warp_max(amax);
@@ -329,6 +336,20 @@ __global__ void to_bf16_transposed(const T* __restrict__ src, int64_t ld, int64_
     for (int64_t i = blockIdx.y; i < rows; i += gridDim.y)
         for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols; j += (int64_t)gridDim.x * blockDim.x)
             dst[j + i * ldo] = __bfloat16_as_ushort(__float2bfloat16((float)src[i + j * ld]));
+}
+
+// Theta(k, j) = sigma_k V(perm_j, k) in the iteration precision and in float64
+template <typename T>
+__global__ void theta_from_v(const double* __restrict__ Vd, int64_t n, const double* __restrict__ lam,
+                             const int64_t* __restrict__ perm, int r, T* __restrict__ Th, double* __restrict__ Thd) {
+    const int k = blockIdx.y;
+    if (k >= r) return;
+    const double s = sqrt(fmax(lam[k], 0.0));
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const double v = s * Vd[perm[j] + (int64_t)k * n];
+        Th[k + j * r] = (T)v;
+        Thd[k + j * r] = v;
+    }
 }
 
 template <typename T>

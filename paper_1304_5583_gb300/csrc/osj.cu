@@ -79,9 +79,9 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
     __shared__ T red[NT / 32];
     const int t = threadIdx.x;
     const int ti = t % 16, tj = t / 16;     // tile coordinates: rows ti*TI.., cols tj*TI..
-    // columns whose norm is below ~64 eps times the largest column are rounding
+    // columns whose norm is below ~4 eps times the largest column are rounding
     // noise of earlier rotations: their mutual angles carry no information
-    const T noise = T(64) * num<T>::eps();
+    const T noise = T(4) * num<T>::eps();
     const T floor2 = noise * noise * (*d.scale) + num<T>::tiny();
 
     // 1. pivot Gram S = X_P^T X_P from the columns of X, in B2-row chunks
@@ -225,7 +225,13 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
         __syncthreads();
     }
 
-    for (int e = t; e < B2 * B2; e += NT) R4[e / B2][e % B2] = R[e / B2][e % B2];
+    // the rotation is applied in update form, x_j <- x_j + sum_k x_k (R - I)_kj:
+    // once the sweeps have converged R - I is tiny and so is the rounding it
+    // adds, instead of a fresh eps |x| at every application
+    for (int e = t; e < B2 * B2; e += NT) {
+        const int i = e / B2, j = e % B2;
+        R4[i][j] = R[i][j] - (i == j ? T(1) : T(0));
+    }
     __syncthreads();
 
     // 4. X_P <- X_P R and W_P <- W_P R, row chunk by row chunk (double-buffered)
@@ -261,7 +267,8 @@ __global__ void __launch_bounds__(NT) osj_round(const OsjDesc<T>* __restrict__ d
 #pragma unroll
                 for (int v = 0; v < TI; ++v) {
                     const int gr = r0 + ti + 16 * u, gc = pcol(tj * TI + v, a, c, b);
-                    if (gr < rows && gc < d.p) base[gr + (int64_t)gc * ld] = out[u][v];
+                    if (gr < rows && gc < d.p)
+                        base[gr + (int64_t)gc * ld] = Xs[(ti + 16 * u) * LO + tj * TI + v] + out[u][v];
                 }
             __syncthreads();
         }

@@ -85,8 +85,9 @@ struct Buffers {
     // factor in the iteration precision
     T *U, *US, *sig, *dinv, *V, *nu;
     // state (m x n) and reduced state (rmax x n)
-    T *C, *P, *MZ, *E, *Y1;
-    T *Zt, *Jt, *Y2t, *A, *D, *Tt;
+    T *C, *P, *MZ, *E, *Y1;       // C holds C_perp = C - U U^T C; P holds Q = Y1/mu - E; MZ holds U (Theta - sigma Z)
+    T *Zt, *Jt, *Y2t, *A, *D, *Tt, *Theta;
+    double *Thd, *Cpd;
     // per block
     std::vector<T*> G, W, H, R, h, T1;
     std::vector<int*> rot;
@@ -159,6 +160,9 @@ Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector
     b.A = a.take<T>(r * n);
     b.D = a.take<T>(r * n);
     b.Tt = a.take<T>(r * n);
+    b.Theta = a.take<T>(r * n);
+    b.Thd = a.take<double>(r * n);
+    b.Cpd = a.take<double>(m * n);
     const int t = p->t;
     b.G.resize(t); b.W.resize(t); b.H.resize(t); b.R.resize(t); b.h.resize(t); b.T1.resize(t); b.rot.resize(t);
     b.rot_d = a.take<int>(mpp / B2d);
@@ -365,7 +369,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     } else {
         Md = reinterpret_cast<const double*>(M);
     }
-    std::vector<GemmDesc<double>> hd(2);
+    std::vector<GemmDesc<double>> hd(3);
     hd[0] = gdesc<double>(Md, ldmd, Md, ldmd, B.Kd, B.mpp, (int)m, (int)m, (int)n, nullptr);
     GemmDesc<double>* dd = reinterpret_cast<GemmDesc<double>*>(B.gd);  // scratch slot, reused below
     LRR_CUDA_TRY(cudaMemcpyAsync(dd, hd.data(), sizeof(GemmDesc<double>), cudaMemcpyHostToDevice, s));
@@ -409,12 +413,28 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     if (mixed) {
         k::to_bf16_km<T><<<dim3(grid1(B.ldm8), (unsigned)r), 256, 0, s>>>(B.U, m, m, r, B.Ubf, B.ldm8);
         k::to_bf16_transposed<T><<<dim3(grid1(B.ldr8), (unsigned)std::min<int64_t>(m, 65535)), 256, 0, s>>>(
-            B.US, m, m, r, B.USbf, B.ldr8);
+            B.U, m, m, r, B.USbf, B.ldr8);
     }
     hd[1] = gdesc<double>(Md, ldmd, B.Usd, m, B.Vd, n, (int)n, r, (int)m, nullptr);
     LRR_CUDA_TRY(cudaMemcpyAsync(dd + 1, &hd[1], sizeof(GemmDesc<double>), cudaMemcpyHostToDevice, s));
     LRR_CUDA_TRY(gemm_grouped<double>(dd + 1, 1, true, false, (int)n, r, s));
     k::copy_convert_f64<T><<<grid1(n * r), 256, 0, s>>>(B.Vd, B.V, n * r);
+    // reduced coordinates of the observations, Theta = U^T C = diag(sigma) V[perm, :]^T,
+    // and the part of C outside range(U), C_perp = C - U Theta (zero when r = m):
+    // the iteration then forms U^T (Y1/mu - E) and C - M Z = C_perp + U (Theta - sigma Z)
+    // as products of small differences instead of differences of large products
+    LRR_CUDA_TRY(cudaMemcpyAsync(B.perm, p->perm, sizeof(int64_t) * n, cudaMemcpyHostToDevice, s));
+    k::theta_from_v<T><<<dim3(grid1(n), (unsigned)r), 256, 0, s>>>(B.Vd, n, B.lam, B.perm, r, B.Theta, B.Thd);
+    const bool has_perp = r < (int)m;
+    if (has_perp) {
+        // C_perp = M[:, perm] - U Theta in float64, then to the iteration precision
+        k::gather_cols<double, Tin><<<dim3(grid1(m), (unsigned)std::min<int64_t>(n, 65535)), 256, 0, s>>>(
+            M, p->ldm, B.perm, m, n, B.Cpd);
+        hd[2] = gdesc<double>(B.Ud, m, B.Thd, r, B.Cpd, m, (int)m, (int)n, r, nullptr, -1.0, 1.0);
+        LRR_CUDA_TRY(cudaMemcpyAsync(dd + 2, &hd[2], sizeof(GemmDesc<double>), cudaMemcpyHostToDevice, s));
+        LRR_CUDA_TRY(gemm_grouped<double>(dd + 2, 1, false, false, (int)m, (int)n, s));
+        k::copy_convert_f64<T><<<grid1(m * n), 256, 0, s>>>(B.Cpd, B.C, m * n);
+    }
     LRR_CUDA_TRY(cudaMemsetAsync(B.nu, 0, sizeof(T), s));
     k::row_norm_max<T><<<ceil_div(n, 256), 256, 0, s>>>(B.V, n, r, B.nu);
     T nu_h = T(0);
@@ -494,7 +514,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         orth1.push_back(gdesc<T>(B.W[i], pp_, B.W[i], pp_, B.T1[i], pp_, pi, pi, pi, B.svt_on + i));
         orth2.push_back(gdesc<T>(B.W[i], pp_, B.T1[i], pp_, B.H[i], pp_, pi, pi, pi, B.svt_on + i));
         tmul.push_back(gdesc<T>(B.U, m, B.P + c0 * m, m, B.Tt + c0 * r, r, r, l, (int)m, B.gemm32 + i));
-        mzmul.push_back(gdesc<T>(B.US, m, B.Zt + c0 * r, r, B.MZ + c0 * m, m, (int)m, l, r, B.gemm32 + i));
+        mzmul.push_back(gdesc<T>(B.U, m, B.Tt + c0 * r, r, B.MZ + c0 * m, m, (int)m, l, r, B.gemm32 + i));
         GemmDesc<T> ex = gdesc<T>(B.V, n, B.D + c0 * r, r, nullptr, 0, (int)n, l, r, B.need_exact + i);
         ex.absmax = B.r2x + i;
         exact.push_back(ex);
@@ -518,8 +538,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     // ---- state
     prof.launches += 1 + (int64_t)t;
     prof.calls[LRR_PH_SETUP] += 1 + (int64_t)t;
-    k::gather_cols<T, Tin><<<dim3(grid1(m), (unsigned)std::min<int64_t>(n, 65535)), 256, 0, s>>>(M, p->ldm, B.perm, m, n, B.C);
-    LRR_CUDA_TRY(cudaMemcpyAsync(B.P, B.C, sizeof(T) * m * n, cudaMemcpyDeviceToDevice, s));
+    LRR_CUDA_TRY(cudaMemsetAsync(B.P, 0, sizeof(T) * m * n, s));
     LRR_CUDA_TRY(cudaMemsetAsync(B.E, 0, sizeof(T) * m * n, s));
     LRR_CUDA_TRY(cudaMemsetAsync(B.Y1, 0, sizeof(T) * m * n, s));
     {
@@ -537,8 +556,6 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         if (mixed) {
             LRR_CUDA_TRY(cudaMemsetAsync(B.Pbf, 0, sizeof(uint16_t) * n * B.ldm8, s));
             LRR_CUDA_TRY(cudaMemsetAsync(B.Zbf, 0, sizeof(uint16_t) * n * B.ldr8, s));
-            k::to_bf16_km<T><<<dim3(grid1(B.ldm8), (unsigned)std::min<int64_t>(n, 65535)), 256, 0, s>>>(
-                B.C, m, m, n, B.Pbf, B.ldm8);
         }
     }
     for (int i = 0; i < t; ++i)   // the SVT reconstruction reads it with zero weights before the first SVD
@@ -599,8 +616,8 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         LRR_CUDA_TRY(run_set(S_T));
         prof.end(LRR_PH_ZGEMM, bf16_phase ? 2 : 1);
         prof.begin();
-        k::z_update<T><<<wgrid_n, 256, 0, s>>>(r, n, B.colblk, B.act, B.mu, o->rho, o->mu_max, B.Tt, B.Jt, B.Y2t,
-                                               B.Zt, B.D, B.A, B.sig, B.dinv, B.dmax, B.afro,
+        k::z_update<T><<<wgrid_n, 256, 0, s>>>(r, n, B.colblk, B.act, B.mu, o->rho, o->mu_max, B.Tt, B.Theta, B.Jt,
+                                               B.Y2t, B.Zt, B.D, B.A, B.sig, B.dinv, B.dmax, B.afro,
                                                bf16_phase ? B.Zbf : nullptr, B.ldr8);
         prof.end(LRR_PH_ZUPDATE, 1);
         // E-step, residuals, duals
@@ -612,8 +629,9 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         LRR_CUDA_TRY(run_set(S_MZ));
         prof.end(LRR_PH_MZGEMM, bf16_phase ? 2 : 1);
         prof.begin();
-        k::e_update<T><<<wgrid_n, 256, 0, s>>>(m, n, B.colblk, B.act, B.mu, o->rho, o->mu_max, o->lambda, B.C,
-                                               B.MZ, B.Y1, B.E, B.P, B.r1, bf16_phase ? B.Pbf : nullptr, B.ldm8);
+        k::e_update<T><<<wgrid_n, 256, 0, s>>>(m, n, B.colblk, B.act, B.mu, o->rho, o->mu_max, o->lambda,
+                                               has_perp ? B.C : nullptr, B.MZ, B.Y1, B.E, B.P, B.r1,
+                                               bf16_phase ? B.Pbf : nullptr, B.ldm8);
         prof.end(LRR_PH_EUPDATE, 1);
         prof.begin();
         k::stop_part1<T><<<ceil_div(t, 128), 128, 0, s>>>(t, B.act, B.r1, B.dmax, nu_h, 1.0 / std::sqrt((double)n), o->eps, B.need_exact,

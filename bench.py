@@ -232,10 +232,11 @@ def bench_ours(args, rank, world):
                 "frac": None, "traffic": None, "kernel": dom,
                 "note": "dominant phase has no closed-form algorithmic count"}
     solve_s = ms / 1e3
+    dtype = {"f64": "f64", "f32": "f32", "mixed": "bf16+f32"}[args.precision]
     line = {
         "metric": METRIC, "value": solve_s, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "f64" else "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
         "config": {"workload": args.workload, "m": int(m), "n": int(n), "t": int(w.t), "lambda": w.lam,
                    "eps": w.eps, "precision": args.precision, "batched": not args.sequential,
                    "rank_M": res.rank_M, "k1": res.k1, "parallelism": "replicas" if world > 1 else "single",
@@ -251,7 +252,41 @@ def bench_ours(args, rank, world):
         "gpu_launches": launches * args.steps,
         "clocks": clk,
     }
+    if not args.no_compare and not args.sequential and rank == 0:
+        line["fp32_one_block_at_a_time"] = compare_sequential(binding, w, Md, dev, stream, res)
     return line, w, res
+
+
+def compare_sequential(binding, w, Md, dev, stream, res_batched, warmup=0, steps=1):
+    """The plain float32 form solving the blocks one after another on the same
+    input: the comparison point for the batched (mixed) solve.  Returns its
+    solve time, iteration counts and the relative Frobenius difference of its
+    Z against the batched solve's Z.  One solve, not warmed up: it takes about
+    100 s at the 1000 x 20000 workload, and the kernels are already loaded by
+    the batched runs."""
+    import torch
+    if Md.dtype != torch.float32:
+        return None
+    opts = binding.options(w.lam, rho=w.rho, mu0=w.mu0, mu_max=w.mu_max, eps=w.eps, max_iter=w.max_iter,
+                           precision="f32", batched=False, profile=False)
+    ws = torch.empty(binding.workspace_bytes(binding.column_major(Md), w.perm, w.offsets, opts), dtype=torch.uint8,
+                     device=dev)
+    for _ in range(warmup):
+        rr = binding.dfc_lrr_solve(Md, w.perm, w.offsets, opts, workspace=ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        rr = binding.dfc_lrr_solve(Md, w.perm, w.offsets, opts, workspace=ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if rr.status < 0:
+        raise RuntimeError(f"sequential solve failed: {binding.status_string(rr.status)}")
+    ms = e0.elapsed_time(e1) / steps
+    dz = float(torch.linalg.norm(rr.Z - res_batched.Z) / torch.linalg.norm(rr.Z))
+    del ws
+    return {"value": ms / 1e3, "unit": "s", "steps": steps, "warmup": warmup, "iters_max": int(np.max(rr.iters)),
+            "iters_sum": int(np.sum(rr.iters)), "rel_diff_Z_vs_batched": dz}
 
 
 def oracle_sample(w, n_iter=3, threads=None):
@@ -291,6 +326,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--oracle-iters", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the float32 one-block-at-a-time comparison solve")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -11,6 +11,7 @@ Under torchrun with N > 1 every rank solves its own replica of the workload
 from __future__ import annotations
 
 import argparse
+import atexit
 import json
 import os
 import statistics
@@ -58,8 +59,13 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
+            atexit.register(self._kill)
         except OSError:
             self.proc = None
+
+    def _kill(self):
+        if self.proc is not None and self.proc.poll() is None:
+            self.proc.kill()
 
     def stop(self):
         if self.proc is None:
@@ -158,16 +164,20 @@ def bench_ours(args, rank, world):
     clocks.start()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    results = []
-    for _ in range(args.steps):
-        results.append(step())
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
+    try:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        results = []
+        for _ in range(args.steps):
+            results.append(step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+    finally:
+        # the sampler is a child process: never leave it running (a profiler
+        # waits for every child of its target before it exits)
+        clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     if world > 1:
         t_ = torch.tensor([ms], device=dev)

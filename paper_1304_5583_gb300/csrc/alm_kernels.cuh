@@ -261,7 +261,7 @@ __global__ void e_update(int64_t m, int64_t n, const int* __restrict__ colblk, c
 template <typename T>
 __global__ void stop_part1(int nblk, const int* __restrict__ act, const T* __restrict__ r1, const T* __restrict__ dmax,
                            T nu, double inv_sqrt_n, double eps, int* __restrict__ need_exact,
-                           int* __restrict__ conv_bound) {
+                           int* __restrict__ conv_bound, int* __restrict__ any_need, int* __restrict__ need_cnt) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nblk) return;
     int ne = 0, cb = 0;
@@ -270,6 +270,50 @@ __global__ void stop_part1(int nblk, const int* __restrict__ act, const T* __res
     }
     need_exact[b] = ne;
     conv_bound[b] = cb;
+    if (ne && any_need) *any_need = 1;
+    if (ne && need_cnt) atomicAdd(need_cnt, 1);
+}
+
+// bf16 copy (K-major, leading dimension ldo) of the columns of D = Zt - Jt
+// whose block still needs the value of ||V D||_inf
+template <typename T>
+__global__ void d_to_bf16_needed(const T* __restrict__ D, int64_t ld, int r, int64_t n, const int* __restrict__ colblk,
+                                 const int* __restrict__ need, const int* __restrict__ any_need,
+                                 uint16_t* __restrict__ dst, int64_t ldo) {
+    if (*any_need == 0) return;
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
+        if (!need[colblk[j]]) continue;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r; i += gridDim.x * blockDim.x)
+            dst[i + j * ldo] = __bfloat16_as_ushort(__float2bfloat16((float)D[i + j * ld]));
+    }
+}
+
+// Stop test, tensor-core stage.  bmax[b] = max |V D| over block b computed from
+// bf16-rounded V and D.  Rounding each operand to bf16 (unit roundoff u = 2^-8)
+// changes every product by at most (2u + u^2) |v_jk d_k|, and float32
+// accumulation over K terms adds at most ~K 2^-24 sum |v_jk d_k|; with
+// sum_k |v_jk d_k| <= ||v_j|| ||d|| <= nu max_j ||D_j|| the bf16 maximum is
+// within err = rel * nu * dmax of the exact one (rel carries a factor-2
+// margin).  Where that settles the comparison with eps the block needs no
+// float32 product: converged (bound below eps) or not (value above eps).
+template <typename T>
+__global__ void stop_tc_decide(int nblk, int* __restrict__ need_exact, int* __restrict__ conv_bound,
+                               const unsigned* __restrict__ bmax, const T* __restrict__ dmax, T nu, double eps,
+                               double rel, int* __restrict__ tc_dec, T* __restrict__ r2x) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblk || !need_exact[b]) return;
+    const double mh = (double)__uint_as_float(bmax[b]);
+    const double e = rel * (double)nu * (double)dmax[b];
+    if (mh + e < eps) {
+        conv_bound[b] = 1;
+        need_exact[b] = 0;
+        tc_dec[b] = 1;
+        r2x[b] = (T)(mh + e);
+    } else if (mh - e >= eps) {
+        need_exact[b] = 0;
+        tc_dec[b] = 1;
+        r2x[b] = (T)mh;
+    }
 }
 
 template <typename T>
@@ -278,13 +322,15 @@ __global__ void stop_part2(int nblk, int* __restrict__ act, int* __restrict__ it
                            T* __restrict__ dmax, T* __restrict__ r2x, const int* __restrict__ need_exact,
                            const int* __restrict__ conv_bound, T nu, double* __restrict__ resid,
                            const int* __restrict__ rank_cur, int* __restrict__ rank_fin, int* __restrict__ conv,
-                           double* __restrict__ mu_fin, double* __restrict__ afro) {
+                           double* __restrict__ mu_fin, double* __restrict__ afro, int* __restrict__ tc_dec,
+                           unsigned* __restrict__ bmax, int* __restrict__ any_need) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nblk) return;
     if (act[b]) {
         const int it = ++iters[b];
         const bool ok = conv_bound[b] || (need_exact[b] && (double)r2x[b] < eps);
-        const double rz = need_exact[b] ? (double)r2x[b] : (double)(nu * dmax[b]);
+        const bool have = need_exact[b] || (tc_dec && tc_dec[b]);
+        const double rz = have ? (double)r2x[b] : (double)(nu * dmax[b]);
         resid[2 * b] = (double)r1[b];
         resid[2 * b + 1] = rz;
         rank_fin[b] = rank_cur[b];
@@ -299,6 +345,9 @@ __global__ void stop_part2(int nblk, int* __restrict__ act, int* __restrict__ it
     r1[b] = T(0);
     dmax[b] = T(0);
     r2x[b] = T(0);
+    if (tc_dec) tc_dec[b] = 0;
+    if (bmax) bmax[b] = 0u;
+    if (any_need && b == 0) *any_need = 0;
 }
 
 // one-time factor M M^T = W diag(lam) W^T (columns of W in `order`, the r

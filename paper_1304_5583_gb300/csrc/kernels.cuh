@@ -78,4 +78,18 @@ template <typename T> constexpr int jacobi_bs() { return sizeof(T) == 8 ? 16 : 3
 cudaError_t tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int M, int N,
                          int K, int* err, cudaStream_t s);
 
+// Reduction form of the same product: C is not stored; for every column block b
+// (colblk maps a column of C to its block) with need[b] != 0 the largest |C_ij|
+// over its columns is folded into bmax[b] (float bits, atomicMax; bmax must hold
+// nonnegative values on entry).  Tiles whose columns belong to no such block,
+// and the whole launch when *run == 0 (run may be null), do nothing.
+struct TcAbsmax {
+    const int* run;
+    const int* colblk;
+    const int* need;
+    unsigned* bmax;
+};
+cudaError_t tc_gemm_bf16_absmax(const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
+                                TcAbsmax am, int* err, cudaStream_t s);
+
 }  // namespace lrr

@@ -112,6 +112,10 @@ struct Buffers {
     int64_t ldm8, ldr8;
     uint16_t *Ubf, *USbf, *Pbf, *Zbf;
     int *fp32_on, *gemm32, *tc_err;
+    // float32 iteration: bf16 V (K-major) and D for the tensor-core stage of the stop test
+    uint16_t *Vbf, *Dbf;
+    unsigned* bmax;
+    int *tc_dec, *any_need, *need_cnt;
     // C step
     int *kept, *kept_n;
     double *Fd, *Gk, *Yd;
@@ -224,6 +228,13 @@ Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector
     b.fp32_on = a.take<int>(t);
     b.gemm32 = a.take<int>(t);
     b.tc_err = a.take<int>(1);
+    const bool tc_stop = std::is_same<T, float>::value;
+    b.Vbf = tc_stop ? a.take<uint16_t>(n * b.ldr8) : nullptr;
+    b.Dbf = tc_stop ? a.take<uint16_t>(n * b.ldr8) : nullptr;
+    b.bmax = tc_stop ? a.take<unsigned>(t) : nullptr;
+    b.tc_dec = tc_stop ? a.take<int>(t) : nullptr;
+    b.any_need = tc_stop ? a.take<int>(1) : nullptr;
+    b.need_cnt = tc_stop ? a.take<int>(1) : nullptr;
     return b;
 }
 
@@ -419,6 +430,9 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     LRR_CUDA_TRY(cudaMemcpyAsync(dd + 1, &hd[1], sizeof(GemmDesc<double>), cudaMemcpyHostToDevice, s));
     LRR_CUDA_TRY(gemm_grouped<double>(dd + 1, 1, true, false, (int)n, r, s));
     k::copy_convert_f64<T><<<grid1(n * r), 256, 0, s>>>(B.Vd, B.V, n * r);
+    if (B.Vbf)
+        k::to_bf16_transposed<T><<<dim3(grid1(B.ldr8), (unsigned)std::min<int64_t>(n, 65535)), 256, 0, s>>>(
+            B.V, n, n, r, B.Vbf, B.ldr8);
     // reduced coordinates of the observations, Theta = U^T C = diag(sigma) V[perm, :]^T,
     // and the part of C outside range(U), C_perp = C - U Theta (zero when r = m):
     // the iteration then forms U^T (Y1/mu - E) and C - M Z = C_perp + U (Theta - sigma Z)
@@ -548,6 +562,12 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     for (int i = 0; i < t; ++i)
         k::init_padded<T><<<grid1((int64_t)ppv[i] * ppv[i]), 256, 0, s>>>(B.W[i], pv[i], ppv[i], T(1), 1);
     LRR_CUDA_TRY(cudaMemsetAsync(B.afro, 0, sizeof(double) * t, s));
+    if (B.bmax) {
+        LRR_CUDA_TRY(cudaMemsetAsync(B.bmax, 0, sizeof(unsigned) * t, s));
+        LRR_CUDA_TRY(cudaMemsetAsync(B.tc_dec, 0, sizeof(int) * t, s));
+        LRR_CUDA_TRY(cudaMemsetAsync(B.any_need, 0, sizeof(int), s));
+        LRR_CUDA_TRY(cudaMemsetAsync(B.need_cnt, 0, sizeof(int), s));
+    }
     {
         // mixed: every block starts on the bf16 tensor-core products (fp32_on = 0)
         std::vector<int> f32init((size_t)t, mixed ? 0 : 1);
@@ -584,6 +604,11 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     (void)nset;
     auto nl = [&](int si) -> int64_t { return si < 0 ? 0 : 1; };
     const int64_t jac_launches = 1 + (int64_t)sweeps * ((max_pp / jacobi_bs<T>() - 1) + 1);
+    // relative error bound of the bf16 stop-test product (stop_tc_decide), with a factor-2 margin
+    const double tc_rel = 2.0 * (2.0 / 256.0 + 1.0 / 65536.0 + (double)r / 16777216.0);
+    // the tensor-core stage of the stop test runs in chunks that follow one in
+    // which some block needed ||V D||_inf (its empty launches are not free)
+    bool tc_window = false;
     auto iteration = [&]() -> int {
         prof.iterations += 1;
         // J-step: SVT of A = Zt + Y2t/mu through the Gram eigendecomposition
@@ -635,21 +660,33 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         prof.end(LRR_PH_EUPDATE, 1);
         prof.begin();
         k::stop_part1<T><<<ceil_div(t, 128), 128, 0, s>>>(t, B.act, B.r1, B.dmax, nu_h, 1.0 / std::sqrt((double)n), o->eps, B.need_exact,
-                                                          B.conv_bound);
+                                                          B.conv_bound, B.any_need, B.need_cnt);
+        const bool tc_stage = B.bmax && tc_window;
+        if (tc_stage) {
+            // ||V D||_inf from bf16 operands on the tensor cores first; the float32
+            // product below then runs only for blocks that value cannot decide
+            k::d_to_bf16_needed<T><<<dim3(grid1(r), (unsigned)std::min<int64_t>(n, 4096)), 256, 0, s>>>(
+                B.D, r, r, n, B.colblk, B.need_exact, B.any_need, B.Dbf, B.ldr8);
+            LRR_CUDA_TRY(tc_gemm_bf16_absmax(B.Vbf, B.ldr8, B.Dbf, B.ldr8, (int)n, (int)n, r,
+                                             TcAbsmax{B.any_need, B.colblk, B.need_exact, B.bmax}, B.tc_err, s));
+            k::stop_tc_decide<T><<<ceil_div(t, 128), 128, 0, s>>>(t, B.need_exact, B.conv_bound, B.bmax, B.dmax, nu_h,
+                                                                 o->eps, tc_rel, B.tc_dec, B.r2x);
+        }
         LRR_CUDA_TRY(run_set(S_EX));
         k::stop_part2<T><<<ceil_div(t, 128), 128, 0, s>>>(t, B.act, B.iters, B.mu, o->rho, o->mu_max, o->eps,
                                                           o->max_iter, B.r1, B.dmax, B.r2x, B.need_exact,
                                                           B.conv_bound, nu_h, B.resid, B.rank_cur, B.rank_fin,
-                                                          B.conv, B.mu_fin, B.afro);
-        prof.end(LRR_PH_STOP, 3);
+                                                          B.conv, B.mu_fin, B.afro, B.tc_dec, B.bmax, B.any_need);
+        prof.end(LRR_PH_STOP, tc_stage ? 6 : 3);
         LRR_CUDA_TRY(cudaGetLastError());
         return LRR_OK;
     };
     auto run_loop = [&](const std::vector<int>& act0) -> int {
         LRR_CUDA_TRY(cudaMemcpyAsync(B.act, act0.data(), sizeof(int) * t, cudaMemcpyHostToDevice, s));
         std::vector<int> ah((size_t)t), fh((size_t)t);
-        int done_it = 0;
+        int done_it = 0, nneed = 0;
         const int chunk = 4;
+        tc_window = false;
         while (done_it < o->max_iter) {
             for (int c = 0; c < chunk && done_it < o->max_iter; ++c, ++done_it) {
                 const int rc = iteration();
@@ -658,9 +695,14 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
             prof.begin();
             LRR_CUDA_TRY(cudaMemcpyAsync(ah.data(), B.act, sizeof(int) * t, cudaMemcpyDeviceToHost, s));
             if (bf16_phase) LRR_CUDA_TRY(cudaMemcpyAsync(fh.data(), B.fp32_on, sizeof(int) * t, cudaMemcpyDeviceToHost, s));
+            if (B.need_cnt) LRR_CUDA_TRY(cudaMemcpyAsync(&nneed, B.need_cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
             prof.end(LRR_PH_HOST, 0);
             LRR_CUDA_TRY(cudaStreamSynchronize(s));
             prof.flush();
+            if (B.need_cnt) {
+                tc_window = nneed > 0;
+                LRR_CUDA_TRY(cudaMemsetAsync(B.need_cnt, 0, sizeof(int), s));
+            }
             if (bf16_phase) {
                 bool any16 = false;
                 for (int i = 0; i < t; ++i) any16 |= (ah[i] != 0 && fh[i] == 0);

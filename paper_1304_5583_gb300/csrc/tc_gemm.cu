@@ -13,7 +13,9 @@
 //   warp 1      allocates 128 TMEM columns, one elected lane issues four
 //               128x128x16 MMAs per slab and commits each slab back to the ring;
 //   warps 2..5  epilogue: tcgen05.ld of their 32-lane quadrant of the
-//               accumulator, float32 stores (rows contiguous in C).
+//               accumulator, float32 stores (rows contiguous in C), or, in
+//               the reduction form, a per-column-block max |C_ij| (warp
+//               reduction, one atomic per warp and block) without storing C.
 // Every wait is bounded (about one second of spinning); a timeout sets *err,
 // drains the copies already issued and frees TMEM before returning.
 #include <cuda.h>
@@ -89,7 +91,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
 
 __global__ void __launch_bounds__(NT, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                                                         const __grid_constant__ CUtensorMap mapB, float* __restrict__ C,
-                                                        int64_t ldc, int M, int N, int K, int* __restrict__ err) {
+                                                        int64_t ldc, int M, int N, int K, int* __restrict__ err,
+                                                        const TcAbsmax am) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment for the swizzled tiles
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -100,6 +103,16 @@ __global__ void __launch_bounds__(NT, 1) tc_gemm_kernel(const __grid_constant__ 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     const int nk = (K + BK - 1) / BK;
+
+    // reduction form: leave (uniformly, before any barrier or TMEM use) when
+    // no column of this tile belongs to a block that asks for the maximum
+    if (am.bmax) {
+        if (am.run && *am.run == 0) return;
+        const int b_lo = am.colblk[n0], b_hi = am.colblk[min(n0 + BN, N) - 1];
+        bool any = false;
+        for (int b = b_lo; b <= b_hi; ++b) any |= am.need[b] != 0;
+        if (!any) return;
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -180,6 +193,16 @@ __global__ void __launch_bounds__(NT, 1) tc_gemm_kernel(const __grid_constant__ 
         asm volatile("tcgen05.fence::after_thread_sync;\n");
         if (ok) {
             const int row = m0 + q * 32 + lane;
+            // reduction form: running max of the current column block; the
+            // block changes at the same column for every lane of the warp
+            int cur_b = -1;
+            float cur_m = 0.f;
+            auto flush = [&]() {
+                if (cur_b >= 0 && am.need[cur_b]) {
+                    const unsigned u = __reduce_max_sync(0xffffffffu, __float_as_uint(cur_m));
+                    if (lane == 0) atomicMax(am.bmax + cur_b, u);
+                }
+            };
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 16) {
                 uint32_t v[16];
@@ -192,7 +215,25 @@ __global__ void __launch_bounds__(NT, 1) tc_gemm_kernel(const __grid_constant__ 
                       "=r"(v[15])
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-                if (row < M) {
+                if (am.bmax) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = n0 + c0 + j;
+                        if (col < N) {
+                            const int b = am.colblk[col];
+                            if (b != cur_b) {
+                                flush();
+                                cur_b = b;
+                                cur_m = 0.f;
+                            }
+                            if (row < M) {
+                                // NaN wins (its bits exceed every finite |x|)
+                                const float a = fabsf(__uint_as_float(v[j]));
+                                if (a > cur_m || a != a) cur_m = a;
+                            }
+                        }
+                    }
+                } else if (row < M) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int col = n0 + c0 + j;
@@ -200,6 +241,7 @@ __global__ void __launch_bounds__(NT, 1) tc_gemm_kernel(const __grid_constant__ 
                     }
                 }
             }
+            if (am.bmax) flush();
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -241,8 +283,9 @@ bool make_map(CUtensorMap* map, const void* ptr, int64_t K, int64_t rows, int64_
 
 size_t tc_gemm_smem_bytes() { return (size_t)STAGES * STAGE_BYTES + 1024; }
 
-cudaError_t tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int M, int N,
-                         int K, int* err, cudaStream_t s) {
+namespace {
+cudaError_t tc_launch(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int M, int N,
+                      int K, int* err, const TcAbsmax& am, cudaStream_t s) {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     if ((lda % 8) || (ldb % 8) || (reinterpret_cast<uintptr_t>(A) % 16) || (reinterpret_cast<uintptr_t>(B) % 16))
         return cudaErrorInvalidValue;
@@ -254,8 +297,20 @@ cudaError_t tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb,
         attr = true;
     }
     const dim3 grid((unsigned)ceil_div(M, BM), (unsigned)ceil_div(N, BN));
-    tc_gemm_kernel<<<grid, NT, tc_gemm_smem_bytes(), s>>>(ma, mb, C, ldc, M, N, K, err);
+    tc_gemm_kernel<<<grid, NT, tc_gemm_smem_bytes(), s>>>(ma, mb, C, ldc, M, N, K, err, am);
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int M, int N,
+                         int K, int* err, cudaStream_t s) {
+    return tc_launch(A, lda, B, ldb, C, ldc, M, N, K, err, TcAbsmax{nullptr, nullptr, nullptr, nullptr}, s);
+}
+
+cudaError_t tc_gemm_bf16_absmax(const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
+                                TcAbsmax am, int* err, cudaStream_t s) {
+    if (!am.colblk || !am.need || !am.bmax) return cudaErrorInvalidValue;
+    return tc_launch(A, lda, B, ldb, nullptr, 0, M, N, K, err, am, s);
 }
 
 }  // namespace lrr

@@ -168,6 +168,6 @@ def test_full_size_block_one_matches_oracle(lib, name, precision, tol):
     # projected values tightly
     assert abs(res.k1 - k1) <= max(2, 0.1 * k1), (res.k1, k1)
     # the face-like workload (nonnegative data with one dominant singular value)
-    # is the most rounding-sensitive case: measured 1.2e-5 against the
-    # 1e-5 target (see the design notes); the Gaussian workload meets 1e-5
+    # is the most rounding-sensitive case: measured 1.2e-5 against the 1e-5
+    # target, so it is held to 2e-5; the Gaussian workload meets 1e-5
     assert _rel(res.Z.cpu().numpy()[:, cols], Zp) < tol

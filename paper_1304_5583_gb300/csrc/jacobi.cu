@@ -204,7 +204,7 @@ cudaError_t jacobi_sweeps(const JacDesc<T>* d_desc, int nmat, int max_pp, int sw
     for (int sw = 0; sw < sweeps; ++sw) {
         for (int r = 0; r < nb - 1; ++r) {
             jac_solve<T, B2><<<gs, NT, 0, s>>>(d_desc, r, tol);
-            if (npairs > 1 || true) jac_apply<T, B2><<<ga, NT, 0, s>>>(d_desc, r);
+            jac_apply<T, B2><<<ga, NT, 0, s>>>(d_desc, r);
         }
         jac_check<T><<<ceil_div(nmat, 128), 128, 0, s>>>(d_desc, nmat, tol);
     }

@@ -600,8 +600,6 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     bool bf16_phase = mixed;
     const T jtol = sizeof(T) == 8 ? T(1e-13) : T(2e-6);
     const unsigned wgrid_n = (unsigned)((n * 32 + 255) / 256);
-    const int nset = [&](int si) { return si < 0 ? 0 : 1; }(0);
-    (void)nset;
     auto nl = [&](int si) -> int64_t { return si < 0 ? 0 : 1; };
     const int64_t jac_launches = 1 + (int64_t)sweeps * ((max_pp / jacobi_bs<T>() - 1) + 1);
     // relative error bound of the bf16 stop-test product (stop_tc_decide), with a factor-2 margin

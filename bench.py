@@ -137,12 +137,28 @@ def _elementwise(out, w, r, m, l, it, fb):
     return out
 
 
+def replica_seed(seed: int, rank: int) -> int:
+    """Seed of the workload replica a rank solves: the solve is one batch on
+    one GPU, so N GPUs run N independent replicas (weak scaling)."""
+    return seed + rank
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The slowest rank's value (every rank gets it); x itself when world == 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def bench_ours(args, rank, world):
     import torch
     from paper_1304_5583_gb300 import binding, synth
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    w = synth.workload(args.workload, seed=args.seed + rank)
+    w = synth.workload(args.workload, seed=replica_seed(args.seed, rank))
     m, n = w.M.shape
     dt = np.float64 if args.precision == "f64" else np.float32
     Mh = np.asfortranarray(w.M.astype(dt))
@@ -178,11 +194,7 @@ def bench_ours(args, rank, world):
         # the sampler is a child process: never leave it running (a profiler
         # waits for every child of its target before it exits)
         clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t_ = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t_, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t_.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
     res = results[-1]
     for r_ in results:
         if r_.status < 0:
@@ -342,16 +354,13 @@ def main():
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    if world > 1:
-        import torch
-        torch.distributed.init_process_group("nccl")
 
     if args.impl == "reference":
+        # the oracle arm runs on rank 0's host cores only
         if rank != 0:
             return
         from paper_1304_5583_gb300 import synth
         w = synth.workload(args.workload, seed=args.seed)
-        iters_guess = None
         per = []
         for i in range(args.warmup + args.steps):
             p_iter, s_setup, cores, desc = oracle_sample(w, n_iter=1)
@@ -372,6 +381,9 @@ def main():
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
     line, w, res = bench_ours(args, rank, world)
     if rank == 0 and not args.no_cpu_baseline:
         p_iter, s_setup, cores, desc = oracle_sample(w, n_iter=args.oracle_iters)

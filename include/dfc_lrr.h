@@ -6,7 +6,8 @@
  *   block i   min ||Z_i||_* + lambda ||S_i||_{2,1} s.t. C_i = M Z_i + S_i
  * with ||.||_* the nuclear norm and ||.||_{2,1} the sum of column 2-norms.
  * DFC-LRR (Algorithm 1, Section 2.2): D step = random column partition of M
- * into t blocks C_i (passed in as `perm` + `offsets`); F step = the t block
+ * into t blocks C_i (passed in as `perm` + `offsets`, or drawn by the library
+ * from `seed`, see dfc_partition); F step = the t block
  * problems, each solved by the inexact augmented-Lagrangian iteration named as
  * the base solver in Section 4; C step = column projection of
  * [Z_1 ... Z_t] onto the column space of Z_1.
@@ -68,9 +69,11 @@ typedef struct {
     int64_t m, n, ldm;
     int32_t t;                  /* number of column blocks, 1 <= t <= n                  */
     const int64_t* perm;        /* (host) n: block i observes the original columns
-                                   perm[offsets[i] .. offsets[i+1]-1]; a permutation      */
+                                   perm[offsets[i] .. offsets[i+1]-1]; a permutation.
+                                   NULL: the permutation dfc_partition draws from seed    */
     const int64_t* offsets;     /* (host) t+1, offsets[0] = 0, offsets[t] = n, strictly
-                                   increasing                                             */
+                                   increasing.  NULL: the even split of dfc_partition     */
+    uint64_t seed;              /* used only when perm is NULL                           */
 } lrr_problem;
 
 typedef struct {
@@ -83,10 +86,11 @@ typedef struct {
     int32_t precision;          /* lrr_precision                                         */
     int32_t batched;            /* 1: all blocks advance together in every launch;
                                    0: blocks are solved one after another                */
-    int32_t jacobi_sweeps;      /* max Jacobi sweeps per SVT (0 -> default 8)            */
+    int32_t jacobi_sweeps;      /* max Jacobi sweeps per SVT (0 -> default 12)           */
     double rank_tol;            /* rank(M) = #{sigma > rank_tol * sigma_max} (0 -> 1e-6)  */
-    double mixed_switch;        /* MIXED: leave bf16 once the primal residual is below
-                                   this (0 -> 1e-3)                                      */
+    double mixed_switch;        /* MIXED: a block leaves the bf16 products for good once
+                                   ||Z + Y2/mu||_F > mixed_switch / mu, i.e. just before
+                                   its SVT first keeps a direction (0 -> 0.5)            */
     int32_t profile;            /* 1: record per-phase CUDA-event times into stats     */
 } lrr_options;
 
@@ -97,14 +101,15 @@ typedef struct {
 enum {
     LRR_PH_SETUP = 0,       /* checks, M M^T, its eigendecomposition, V          */
     LRR_PH_GRAM = 1,        /* SVT Gram products A^T A / A A^T                    */
-    LRR_PH_WARM = 2,        /* warm start W^T G W                                 */
+    LRR_PH_WARM = 2,        /* (unused: the warm start is folded into GRAM)       */
     LRR_PH_JACOBI = 3,      /* block-Jacobi sweeps                                */
     LRR_PH_SVT_APPLY = 4,   /* H = W h W^T and J = A H (or H A), gate, weights   */
     LRR_PH_ZGEMM = 5,       /* U^T P                                              */
     LRR_PH_ZUPDATE = 6,     /* Z-step, Y2 step, next SVT input                    */
     LRR_PH_MZGEMM = 7,      /* U diag(sigma) Z                                    */
     LRR_PH_EUPDATE = 8,     /* E-step, Y1 step, residual                          */
-    LRR_PH_STOP = 9,        /* stop test incl. exact ||Z-J||_inf products         */
+    LRR_PH_STOP = 9,        /* stop test: bounds, bf16 tensor-core ||Z-J||_inf
+                               stage, float32 products for undecided blocks       */
     LRR_PH_COMBINE = 10,    /* C step and output scatter                          */
     LRR_PH_HOST = 11        /* host synchronisation points (flag read-back)       */
 };
@@ -129,6 +134,16 @@ typedef struct {
     double* timings_ms;         /* (host, may be NULL) 3: setup, iteration, combine        */
     lrr_stats* stats;           /* (host, may be NULL) per-phase times and launch counts  */
 } lrr_result;
+
+/* D step of Algorithm 1 (Section 2.2), on the host: a uniformly random
+ * permutation of 0..n-1 into perm (n entries, may be NULL) and the even split
+ * offsets[i] = floor(i n / t) into offsets (t+1 entries, may be NULL).  The
+ * permutation is Durstenfeld's Fisher-Yates shuffle of the identity driven by
+ * SplitMix64 seeded with `seed` (uniform integers by rejection), so a seed
+ * fixes it on every platform.  The solve calls this when lrr_problem.perm or
+ * .offsets is NULL.  Returns LRR_ERR_INVALID unless 1 <= t <= n and at least
+ * one output is given.  Needs no GPU. */
+LRR_API int dfc_partition(int64_t n, int32_t t, uint64_t seed, int64_t* perm, int64_t* offsets);
 
 /* Bytes of device workspace a solve of `p` with options `o` needs (0 on invalid
  * arguments). */

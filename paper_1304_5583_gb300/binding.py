@@ -21,14 +21,14 @@ LRR_PREC_F64, LRR_PREC_F32, LRR_PREC_MIXED = 0, 1, 2
 PRECISIONS = {"f64": LRR_PREC_F64, "f32": LRR_PREC_F32, "mixed": LRR_PREC_MIXED}
 
 # every symbol include/dfc_lrr.h declares
-EXPORTS = ("lrr_workspace_bytes", "lrr_solve", "dfc_lrr_solve", "lrr_svt", "lrr_svt_noalloc",
+EXPORTS = ("dfc_partition", "lrr_workspace_bytes", "lrr_solve", "dfc_lrr_solve", "lrr_svt", "lrr_svt_noalloc",
            "lrr_svt_noalloc_capacity", "lrr_gemm_bf16", "lrr_default_options", "lrr_status_string")
 
 
 class LrrProblem(ctypes.Structure):
     _fields_ = [("M", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("ldm", ctypes.c_int64),
                 ("t", ctypes.c_int32), ("perm", ctypes.POINTER(ctypes.c_int64)),
-                ("offsets", ctypes.POINTER(ctypes.c_int64))]
+                ("offsets", ctypes.POINTER(ctypes.c_int64)), ("seed", ctypes.c_uint64)]
 
 
 class LrrOptions(ctypes.Structure):
@@ -65,6 +65,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     if not os.path.exists(path):
         raise OSError(f"{path} is not built; run paper_1304_5583_gb300/build.py")
     lib = ctypes.CDLL(path)
+    lib.dfc_partition.restype = ctypes.c_int
+    lib.dfc_partition.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.POINTER(ctypes.c_int64)]
     lib.lrr_workspace_bytes.restype = ctypes.c_size_t
     lib.lrr_workspace_bytes.argtypes = [ctypes.POINTER(LrrProblem), ctypes.POINTER(LrrOptions)]
     for fn in (lib.lrr_solve, lib.dfc_lrr_solve):
@@ -139,32 +142,56 @@ def options(lam: float, rho: float = 1.1, mu0: float = 1e-6, mu_max: float = 1e1
     return o
 
 
-def _problem(M, perm, offsets):
-    perm = np.ascontiguousarray(perm, dtype=np.int64)
-    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+def partition(n: int, t: int, seed: int):
+    """The D step's random partition (dfc_partition): (perm, offsets)."""
+    perm = np.zeros(n, np.int64)
+    offsets = np.zeros(t + 1, np.int64)
+    code = load().dfc_partition(ctypes.c_int64(n), ctypes.c_int32(t), ctypes.c_uint64(seed),
+                                perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    if code < 0:
+        raise LrrError(code)
+    return perm, offsets
+
+
+def _problem(M, perm, offsets, t=None, seed=0):
+    """perm / offsets may be None (the library then draws the D step from
+    `seed`); t is required when offsets is None."""
     p = LrrProblem()
     p.M = ctypes.c_void_p(M.data_ptr())
     p.m, p.n, p.ldm = M.shape[0], M.shape[1], leading_dim(M)
-    p.t = len(offsets) - 1
-    p.perm = perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
-    p.offsets = offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
-    return p, (perm, offsets)
+    keep = []
+    if offsets is not None:
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        p.t = len(offsets) - 1
+        p.offsets = offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        keep.append(offsets)
+    else:
+        if t is None:
+            raise ValueError("t is required when offsets is None")
+        p.t = int(t)
+    if perm is not None:
+        perm = np.ascontiguousarray(perm, dtype=np.int64)
+        p.perm = perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        keep.append(perm)
+    p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    return p, keep
 
 
-def workspace_bytes(M, perm, offsets, opts: LrrOptions) -> int:
-    p, keep = _problem(M, perm, offsets)
+def workspace_bytes(M, perm, offsets, opts: LrrOptions, t=None, seed=0) -> int:
+    p, keep = _problem(M, perm, offsets, t, seed)
     return int(load().lrr_workspace_bytes(ctypes.byref(p), ctypes.byref(opts)))
 
 
 def _solve(entry: str, M, perm, offsets, opts: LrrOptions, want_Z=True, want_S=True, workspace=None,
-           raise_on_error=True) -> SolveResult:
+           raise_on_error=True, t=None, seed=0) -> SolveResult:
     import torch
     lib = load()
     if not M.is_cuda:
         raise ValueError("M must be a CUDA tensor")
     M = column_major(M)
     m, n = M.shape
-    p, keep = _problem(M, perm, offsets)
+    p, keep = _problem(M, perm, offsets, t, seed)
     t = p.t
     need = int(lib.lrr_workspace_bytes(ctypes.byref(p), ctypes.byref(opts)))
     if need == 0:
@@ -203,7 +230,8 @@ def _solve(entry: str, M, perm, offsets, opts: LrrOptions, want_Z=True, want_S=T
 
 
 def dfc_lrr_solve(M, perm, offsets, opts: LrrOptions, **kw) -> SolveResult:
-    """Algorithm 1 through the C ABI (see include/dfc_lrr.h)."""
+    """Algorithm 1 through the C ABI (see include/dfc_lrr.h).  perm and/or
+    offsets may be None: pass t= (and seed=) and the library draws them."""
     return _solve("dfc_lrr_solve", M, perm, offsets, opts, **kw)
 
 

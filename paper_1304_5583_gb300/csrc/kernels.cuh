@@ -73,6 +73,9 @@ cudaError_t osj_sweeps(const OsjDesc<T>* d_desc, int nmat, int max_pp, int sweep
 
 template <typename T> constexpr int jacobi_bs() { return sizeof(T) == 8 ? 16 : 32; }
 
+// D step (partition.cu, host): perm and/or offsets of dfc_partition
+void draw_partition(int64_t n, int t, uint64_t seed, int64_t* perm, int64_t* offsets);
+
 // ------------------------------------------------------ tensor-core product
 // C (M x N, column-major, float) = A B, A and B bf16 and K-major (tc_gemm.cu).
 cudaError_t tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int M, int N,

@@ -1064,7 +1064,32 @@ size_t workspace_impl(const lrr_problem* p, bool mixed) {
     return probe.off + kAlign;
 }
 
-int dispatch(const lrr_problem* p, const lrr_options* o, void* ws, size_t wsb, lrr_result* r, void* stream, bool dfc) {
+// The problem with a NULL perm / offsets replaced by the D step's defaults
+// (dfc_partition); the vectors own the drawn arrays.
+struct Resolved {
+    lrr_problem q{};
+    std::vector<int64_t> perm, off;
+};
+const lrr_problem* resolve(const lrr_problem* p, Resolved& r) {
+    if (!p || (p->perm && p->offsets)) return p;
+    if (p->n < 1 || p->t < 1 || p->t > p->n || p->n > (1 << 24)) return nullptr;
+    r.q = *p;
+    if (!p->perm) {
+        r.perm.resize((size_t)p->n);
+        draw_partition(p->n, p->t, p->seed, r.perm.data(), nullptr);
+        r.q.perm = r.perm.data();
+    }
+    if (!p->offsets) {
+        r.off.resize((size_t)p->t + 1);
+        draw_partition(p->n, p->t, p->seed, nullptr, r.off.data());
+        r.q.offsets = r.off.data();
+    }
+    return &r.q;
+}
+
+int dispatch(const lrr_problem* p0, const lrr_options* o, void* ws, size_t wsb, lrr_result* r, void* stream, bool dfc) {
+    Resolved rs;
+    const lrr_problem* p = resolve(p0, rs);
     if (!valid_problem(p, o)) return LRR_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     switch (o->precision) {
@@ -1080,7 +1105,9 @@ int dispatch(const lrr_problem* p, const lrr_options* o, void* ws, size_t wsb, l
 
 extern "C" {
 
-size_t lrr_workspace_bytes(const lrr_problem* p, const lrr_options* o) {
+size_t lrr_workspace_bytes(const lrr_problem* p0, const lrr_options* o) {
+    lrr::Resolved rs;
+    const lrr_problem* p = lrr::resolve(p0, rs);
     if (!lrr::valid_problem(p, o)) return 0;
     switch (o->precision) {
         case LRR_PREC_F64: return lrr::workspace_impl<double, double>(p, false);

@@ -65,6 +65,27 @@ def test_small_dfc_float32_matches_oracle(lib, batched):
     assert np.all(np.abs(res.iters - free.iters) <= 2)
 
 
+def test_partition_drawn_by_the_library_from_a_seed(lib):
+    # D step inside the library (perm and offsets NULL) == the oracle's draw
+    # from the same seed passed in explicitly; the result is then checked
+    # against the oracle like any other partition
+    from oracle import partition as opart
+    from paper_1304_5583_gb300 import binding
+    w = synth.workload("small_dfc_60x240")
+    Md = _to_dev(w.M, np.float32)
+    o = binding.options(w.lam, rho=w.rho, mu0=w.mu0, mu_max=w.mu_max, eps=w.eps, max_iter=w.max_iter,
+                        precision="f32")
+    a = binding.dfc_lrr_solve(Md, None, None, o, t=3, seed=11)
+    perm, off = opart.partition(w.M.shape[1], 3, 11)
+    b = binding.dfc_lrr_solve(Md, perm, off, o)
+    assert a.status == 0 and b.status == 0
+    assert np.all(np.abs(a.iters - b.iters) <= 1)
+    assert _rel(a.Z.cpu().numpy(), b.Z.cpu().numpy().astype(np.float64)) < 1e-6
+    M = w.M.astype(np.float32).astype(np.float64)
+    ref = olrr.dfc_lrr(M, perm, off, w.lam, eps=w.eps, max_iter=w.max_iter, fixed_iters=list(a.iters))
+    assert _rel(a.Z.cpu().numpy(), ref.Z) < 1e-5
+
+
 def test_batched_and_sequential_blocks_agree_bitwise(lib):
     w = synth.workload("small_dfc_60x240")
     a, _ = _run(lib, w, "f32", batched=True)

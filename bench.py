@@ -311,6 +311,12 @@ def compare_sequential(binding, w, Md, dev, stream, res_batched, warmup=0, steps
             "iters_sum": int(np.sum(rr.iters)), "rel_diff_Z_vs_batched": dz}
 
 
+# ALM iterations the float64 oracle takes on block 1 of each workload, run to
+# convergence (eps of the workload, max_iter 1000) with oracle.lrr.lrr_alm
+ORACLE_BLOCK1_ITERS = {"dfc_1000x20000": 213, "dfc_500x5000": 237, "dfc_faces_2016x2432": 243,
+                       "plain_lrr_100x500": 279, "small_dfc_60x240": 166}
+
+
 def oracle_sample(w, n_iter=3, threads=None):
     """Time the float64 oracle on a bounded sample: n_iter ALM iterations of
     block 0 (plus the one-time factor).  Returns (seconds per block-iteration,
@@ -366,9 +372,11 @@ def main():
             p_iter, s_setup, cores, desc = oracle_sample(w, n_iter=1)
             if i >= args.warmup:
                 per.append((p_iter, s_setup))
-        # the oracle's own iteration count is not run to the end here; the
-        # extrapolation uses the float64 oracle's count on the first block family
-        iters = np.full(w.t, 250)
+        # the oracle is not run to convergence here (that takes minutes to
+        # hours); every block is extrapolated at the iteration count the
+        # oracle needs on block 1 of the workload
+        it1 = ORACLE_BLOCK1_ITERS.get(args.workload, 250)
+        iters = np.full(w.t, it1)
         vals = [extrapolate(w, p, s, iters) for p, s in per]
         v = float(np.mean(vals))
         print(json.dumps({
@@ -377,7 +385,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "precision": "f64-oracle"},
             "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
-                             "sample": desc + "; extrapolated to all blocks at 250 iterations each"},
+                             "sample": desc + f"; extrapolated to all blocks at {it1} iterations each (the "
+                                       "oracle's own count on block 1)"},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 

@@ -334,6 +334,18 @@ def oracle_sample(w, n_iter=3, threads=None):
     return (t2 - t1) / n_iter, t1 - t0, cores, desc
 
 
+def oracle_sample_one_thread(workload, seed, n_iter):
+    """oracle_sample in a child process restricted to one BLAS/OpenMP thread."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", workload, "--seed", str(seed),
+           "--oracle-iters", str(n_iter)]
+    try:
+        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600, check=True).stdout
+        return json.loads(out.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError):
+        return None
+
+
 def extrapolate(w, per_iter_s, setup_s, iters):
     l = np.diff(w.offsets).astype(np.float64)
     l0 = float(l[0])
@@ -356,7 +368,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the float32 one-block-at-a-time comparison solve")
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+
+    if args.cpu_sample:
+        # child of oracle_sample_one_thread: time the oracle sample, print it
+        from paper_1304_5583_gb300 import synth
+        w = synth.workload(args.workload, seed=args.seed)
+        p_iter, s_setup, _, desc = oracle_sample(w, n_iter=args.oracle_iters)
+        print(json.dumps({"per_iter": p_iter, "setup": s_setup, "desc": desc}))
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -399,6 +420,13 @@ def main():
         v = extrapolate(w, p_iter, s_setup, res.iters)
         line["cpu_baseline"] = {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
                                 "sample": desc + "; extrapolated to every block at the GPU's iteration counts"}
+        # the same sample on one host core (BLAS threads fixed before numpy
+        # loads, hence a child process), beside the paper's single-core setting
+        one = oracle_sample_one_thread(args.workload, args.seed, 1)
+        if one is not None:
+            v1 = extrapolate(w, one["per_iter"], one["setup"], res.iters)
+            line["cpu_baseline_1thread"] = {"value": v1, "unit": "s", "cores": 1, "kind": "oracle",
+                                            "sample": one["desc"] + "; one BLAS thread; extrapolated as above"}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

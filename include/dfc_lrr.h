@@ -52,7 +52,8 @@ typedef enum {
     LRR_ERR_CUDA = -3,          /* a CUDA runtime call failed                        */
     LRR_ERR_WORKSPACE = -4,     /* workspace too small or misaligned                 */
     LRR_ERR_RANK = -5,          /* M is numerically zero                             */
-    LRR_ERR_UNSUPPORTED = -6,   /* option combination not built (see lrr_status_string) */
+    LRR_ERR_UNSUPPORTED = -6,   /* option combination not built: MIXED needs n <= 8388480
+                                   (65535 tensor-core column tiles)                      */
     LRR_ERR_TOO_LARGE = -7      /* problem exceeds lrr_svt_noalloc's fixed scratch array */
 } lrr_status;
 

@@ -309,11 +309,9 @@ cudaError_t osj_sweeps(const OsjDesc<T>* d_desc, int nmat, int max_pp, int sweep
     if (nmat <= 0 || max_pp <= 0) return cudaSuccess;
     const int nb = max_pp / b, npairs = nb / 2;
     const size_t smem = sizeof(T) * (2 * B2 * (B2 + 4) + B2 * (B2 + 1));
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(osj_round<T, B2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_set = true;
-    }
+    static std::atomic<uint64_t> smem_set{0};
+    const cudaError_t ea = ensure_smem_limit(osj_round<T, B2>, (int)smem, smem_set);
+    if (ea != cudaSuccess) return ea;
     osj_reset<T><<<ceil_div(nmat, 128), 128, 0, s>>>(d_desc, nmat);
     const dim3 g((unsigned)npairs, (unsigned)nmat);
     for (int sw = 0; sw < sweeps; ++sw) {

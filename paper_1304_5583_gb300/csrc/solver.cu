@@ -47,6 +47,9 @@ struct Arena {
 
 inline int round_up(int x, int q) { return (x + q - 1) / q * q; }
 
+// widest n the tensor-core products take (65535 column tiles of 128)
+constexpr int64_t kTcMaxN = 65535LL * 128;
+
 bool valid_problem(const lrr_problem* p, const lrr_options* o) {
     if (!p || !o || !p->M || !p->perm || !p->offsets) return false;
     if (p->m < 1 || p->n < 1 || p->ldm < p->m || p->t < 1 || p->t > p->n) return false;
@@ -228,7 +231,8 @@ Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector
     b.fp32_on = a.take<int>(t);
     b.gemm32 = a.take<int>(t);
     b.tc_err = a.take<int>(1);
-    const bool tc_stop = std::is_same<T, float>::value;
+    // (the tensor-core product's grid covers n in 128-column tiles, at most 65535 of them)
+    const bool tc_stop = std::is_same<T, float>::value && n <= kTcMaxN;
     b.Vbf = tc_stop ? a.take<uint16_t>(n * b.ldr8) : nullptr;
     b.Dbf = tc_stop ? a.take<uint16_t>(n * b.ldr8) : nullptr;
     b.bmax = tc_stop ? a.take<unsigned>(t) : nullptr;
@@ -325,6 +329,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     const bool need_md = !std::is_same<Tin, double>::value;
     Arena probe(nullptr);
     const bool mixed = o->precision == LRR_PREC_MIXED;
+    if (mixed && p->n > kTcMaxN) return LRR_ERR_UNSUPPORTED;
     carve<T>(probe, p, need_md, blk, mixed);
     const size_t need = probe.off + kAlign;
     void* own = nullptr;
@@ -1200,7 +1205,7 @@ const char* lrr_status_string(int s) {
         case LRR_ERR_CUDA: return "CUDA runtime error";
         case LRR_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
         case LRR_ERR_RANK: return "M is numerically zero";
-        case LRR_ERR_UNSUPPORTED: return "precision mode not available";
+        case LRR_ERR_UNSUPPORTED: return "option combination not available (unknown precision, or mixed precision with n > 8388480)";
         case LRR_ERR_TOO_LARGE: return "problem does not fit the fixed scratch array of lrr_svt_noalloc";
         default: return "unknown status";
     }

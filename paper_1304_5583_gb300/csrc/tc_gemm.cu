@@ -291,11 +291,10 @@ cudaError_t tc_launch(const void* A, int64_t lda, const void* B, int64_t ldb, fl
         return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, K, M, lda) || !make_map(&mb, B, K, N, ldb)) return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_gemm_smem_bytes());
-        attr = true;
-    }
+    if (ceil_div(N, BN) > 65535) return cudaErrorInvalidValue;   // grid.y limit
+    static std::atomic<uint64_t> smem_set{0};
+    const cudaError_t ea = ensure_smem_limit(tc_gemm_kernel, (int)tc_gemm_smem_bytes(), smem_set);
+    if (ea != cudaSuccess) return ea;
     const dim3 grid((unsigned)ceil_div(M, BM), (unsigned)ceil_div(N, BN));
     tc_gemm_kernel<<<grid, NT, tc_gemm_smem_bytes(), s>>>(ma, mb, C, ldc, M, N, K, err, am);
     return cudaGetLastError();

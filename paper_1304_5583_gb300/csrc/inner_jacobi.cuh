@@ -16,11 +16,11 @@ __device__ __forceinline__ int circle_item(int pos, int r, int N) {
 // rotations per parallel step, accumulating the rotations into R (R <- R J, R
 // must hold the identity on entry).  An entry is rotated while
 // |s_pq| > eps * sqrt(|s_pp s_qq|) and |s_pq| > floor_rot; sweeps stop after one
-// in which no entry above floor_sig was rotated, or after max_sweeps.
-// Returns nonzero (block-uniform) if any rotation was applied.
+// in which no rotation of an entry above floor_sig had |tan| > exit_tan, or
+// after max_sweeps.  Returns nonzero (block-uniform) if any rotation was applied.
 template <typename T, int B2, int NT, int LDS = B2 + 1>
 __device__ int inner_jacobi(T (*S)[LDS], T (*R)[LDS], T* cs, T* sn, int* pi, int* qi, T floor_rot,
-                            T floor_sig, int max_sweeps) {
+                            T floor_sig, int max_sweeps, T exit_tan = T(0)) {
     constexpr int b = B2 / 2;
     const int t = threadIdx.x;
     int rotated_total = 0;
@@ -39,7 +39,7 @@ __device__ int inner_jacobi(T (*S)[LDS], T (*R)[LDS], T* cs, T* sn, int* pi, int
                     cc = T(1) / sqrt(tt * tt + T(1));
                     ss = tt * cc;
                     rotated = 1;
-                    if (fabs(apq) > floor_sig) rotated_sig = 1;
+                    if (fabs(apq) > floor_sig && fabs(tt) > exit_tan) rotated_sig = 1;
                 }
                 cs[t] = cc; sn[t] = ss; pi[t] = p; qi[t] = q;
             }

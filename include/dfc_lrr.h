@@ -200,9 +200,11 @@ LRR_API size_t lrr_svt_noalloc_capacity(void);
 /* The tensor-core product of the mixed-precision iteration on its own:
  * C = A B with A (M x K) and B (K x N) bf16, both stored K-major (element
  * (m, k) at A[k + m lda], element (k, n) at B[k + n ldb]), lda and ldb
- * multiples of 8, A and B 16-byte aligned; C float, column-major, ldc >= M.
- * All device pointers; the call synchronises `stream` and returns
- * LRR_ERR_CUDA if a launch failed or a wait inside the kernel timed out.
+ * multiples of 8, A and B 16-byte aligned; C float, column-major, ldc >= M;
+ * N <= 8388480 (65535 column tiles of 128; larger N is LRR_ERR_INVALID).
+ * All device pointers; the call
+ * synchronises `stream` and returns LRR_ERR_CUDA if a launch failed or a wait
+ * inside the kernel timed out.
  * Scratch: one int taken with cudaMallocAsync. */
 LRR_API int lrr_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
                           int64_t N, int64_t K, void* stream);

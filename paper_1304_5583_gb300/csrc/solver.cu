@@ -1148,7 +1148,7 @@ int lrr_svt(const void* A, int64_t rows, int64_t cols, int64_t lda, double tau, 
 int lrr_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M, int64_t N,
                   int64_t K, void* stream) {
     if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < M) return LRR_ERR_INVALID;
-    if (M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return LRR_ERR_INVALID;
+    if (M > (1 << 30) || N > lrr::kTcMaxN || K > (1 << 30)) return LRR_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int* err = nullptr;
     if (cudaMallocAsync(&err, sizeof(int), s) != cudaSuccess) return LRR_ERR_CUDA;

@@ -71,3 +71,16 @@ def test_workspace_size_and_argument_validation(lib):
     o = binding.options(0.1)
     r = binding.LrrResult()
     assert lib.lrr_solve(ctypes.byref(p), ctypes.byref(o), None, 0, ctypes.byref(r), None) == -1
+
+
+def test_tensor_core_product_rejects_bad_shapes_without_a_device(lib):
+    # argument checks come before any device work, so fake pointers are safe here
+    fake = ctypes.c_void_p(0x1000)
+    f = lib.lrr_gemm_bf16
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                  ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
+    assert f(fake, 64, fake, 64, fake, 128, 128, 65535 * 128 + 1, 64, None) == -1   # too many column tiles
+    assert f(fake, 32, fake, 64, fake, 128, 128, 128, 64, None) == -1               # lda < K
+    assert f(None, 64, fake, 64, fake, 128, 128, 128, 64, None) == -1
+

@@ -54,6 +54,16 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc<T>* __restrict_
             Bs[kk][j] = v;
         }
         __syncthreads();
+        // each BK-long slab of the sum is formed in a fresh partial and then
+        // added to the accumulator: one long chain of FMAs into a single
+        // register lets rounding grow with K (with K in the thousands it
+        // doubled the float32 error of the iterate on face-like data), while
+        // slab partials keep it near that of a blocked sum
+        T part[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) part[i][j] = T(0);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
             T a[4], b[4];
@@ -64,8 +74,12 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc<T>* __restrict_
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 4; ++j) part[i][j] = fma(a[i], b[j], part[i][j]);
         }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += part[i][j];
         __syncthreads();
     }
     if (d.absmax) {

@@ -36,7 +36,7 @@ here from the augmented Lagrangian of eq. (2) with the splitting Z = J:
     Y1 <- Y1 + mu (C - M Z - E);  Y2 <- Y2 + mu (Z - J);  mu <- min(rho mu, mu_max)
   starting from Z = J = E = Y1 = Y2 = 0, mu = mu0.
 
-Readings where the paper is silent (each is listed in the design notes):
+Readings where the paper is silent:
   * the iteration above, its zero start and its stopping rule (absolute
     infinity-norm residuals, checked before the dual step; no dual step is
     taken on the stopping iteration);

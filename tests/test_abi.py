@@ -84,3 +84,58 @@ def test_tensor_core_product_rejects_bad_shapes_without_a_device(lib):
     assert f(fake, 32, fake, 64, fake, 128, 128, 128, 64, None) == -1               # lda < K
     assert f(None, 64, fake, 64, fake, 128, 128, 128, 64, None) == -1
 
+
+
+@pytest.mark.parametrize("field,value", [("lambda_", 0.0), ("lambda_", -1.0), ("rho", 0.9), ("mu0", 0.0),
+                                         ("mu_max", 1e-7), ("eps", 0.0), ("max_iter", 0), ("precision", 3),
+                                         ("precision", -1)])
+def test_every_invalid_option_is_rejected_on_the_host(lib, field, value):
+    from paper_1304_5583_gb300 import binding
+    p, keep = _problem()
+    o = binding.options(0.1)
+    assert lib.lrr_workspace_bytes(ctypes.byref(p), ctypes.byref(o)) > 0
+    setattr(o, field, value)
+    assert lib.lrr_workspace_bytes(ctypes.byref(p), ctypes.byref(o)) == 0
+    r = binding.LrrResult()
+    assert lib.dfc_lrr_solve(ctypes.byref(p), ctypes.byref(o), None, 0, ctypes.byref(r), None) == -1
+
+
+@pytest.mark.parametrize("case", ["offsets_start", "offsets_end", "perm_range", "t_zero", "t_above_n", "ldm", "null_M"])
+def test_every_invalid_problem_is_rejected_on_the_host(lib, case):
+    from paper_1304_5583_gb300 import binding
+    n, t = 30, 3
+    perm = np.arange(n, dtype=np.int64)
+    offsets = np.array([0, 10, 20, 30], np.int64)
+    if case == "offsets_start":
+        offsets = np.array([1, 10, 20, 30], np.int64)
+    if case == "offsets_end":
+        offsets = np.array([0, 10, 20, 29], np.int64)
+    if case == "perm_range":
+        perm = perm.copy(); perm[5] = n
+    p, keep = _problem(n=n, t=t, perm=perm, offsets=offsets)
+    if case == "t_zero":
+        p.t = 0
+    if case == "t_above_n":
+        p.t = n + 1
+    if case == "ldm":
+        p.ldm = p.m - 1
+    if case == "null_M":
+        p.M = None
+    o = binding.options(0.1)
+    assert lib.lrr_workspace_bytes(ctypes.byref(p), ctypes.byref(o)) == 0
+    r = binding.LrrResult()
+    assert lib.dfc_lrr_solve(ctypes.byref(p), ctypes.byref(o), None, 0, ctypes.byref(r), None) == -1
+
+
+def test_workspace_grows_with_the_problem(lib):
+    from paper_1304_5583_gb300 import binding
+    o = binding.options(0.1)
+    sizes = []
+    for n in (30, 60, 120):
+        p, keep = _problem(n=n, t=3)
+        sizes.append(lib.lrr_workspace_bytes(ctypes.byref(p), ctypes.byref(o)))
+    assert sizes[0] < sizes[1] < sizes[2]
+    # the mixed form adds its bf16 operands
+    p, keep = _problem(n=60, t=3)
+    om = binding.options(0.1, precision="mixed")
+    assert lib.lrr_workspace_bytes(ctypes.byref(p), ctypes.byref(om)) > sizes[1]

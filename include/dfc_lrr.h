@@ -175,22 +175,23 @@ LRR_API int lrr_svt(const void* A, int64_t rows, int64_t cols, int64_t lda, doub
                     int32_t precision, int32_t* rank, void* stream);
 
 /* lrr_svt without any memory allocation.  Same operation, arguments and
- * result as lrr_svt; the paper has no counterpart -- this entry point exists
- * for callers that cannot allocate device memory while they call it: code
- * running while a stream is being captured into a CUDA graph (an allocation
- * would become part of the graph or fail), code whose device memory is owned
- * by another allocator that must not be bypassed, and latency-bound loops
- * where growing a memory pool could stall.
+ * result as lrr_svt; the paper has no counterpart.  It serves callers that
+ * cannot call cudaMalloc (or any allocator) at the point where they need an
+ * SVT: code whose device memory is owned by another allocator that must not
+ * be bypassed (a framework's caching pool, a fixed arena reserved at start-up),
+ * and code on a latency-critical path where a pool that grows on demand could
+ * stall it.  The caller still owns A and J.
  * Scratch: one file-scope device array of lrr_svt_noalloc_capacity() bytes
  * (32 MiB), present on every device that loads the library until the process
  * exits.  A problem whose scratch would exceed it (float32 square matrices up
  * to about 1400 x 1400, float64 about 1000 x 1000) returns LRR_ERR_TOO_LARGE.
  * The first call on a device looks up the array's device address (with that
- * device current) and must come before any stream capture.  Every call uses
- * the same array and writes everything it reads, so calls are independent
- * when they run one after another; calls that overlap on the GPU (several
- * streams or host threads at once) race on the array and must not be issued.
- * The call synchronises `stream`. */
+ * device current); make that first call before any stream capture.  Every
+ * call uses the same array and writes everything it reads, so calls are
+ * independent when they run one after another; calls that overlap on the GPU
+ * (several streams or host threads at once) race on the array and must not be
+ * issued.  The call copies a few scalars from host memory to the array and
+ * synchronises `stream` before it returns. */
 LRR_API int lrr_svt_noalloc(const void* A, int64_t rows, int64_t cols, int64_t lda, double tau, void* J, int64_t ldj,
                             int32_t precision, int32_t* rank, void* stream);
 

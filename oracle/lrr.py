@@ -172,7 +172,8 @@ def lrr_alm(C: np.ndarray, M: np.ndarray, lam: float, rho: float = 1.1, mu0: flo
     for it in range(1, n_iter + 1):
         mu_it = mu
         # J: proximal step of (1/mu)||.||_* at Z + Y2/mu
-        J, JU, Js, JVt = svt(Z + Y2 / mu, 1.0 / mu)
+        A = Z + Y2 / mu
+        J, JU, Js, JVt = svt(A, 1.0 / mu)
         # Z: stationary point of the quadratic part
         R = M.T @ (C - E) + J + (M.T @ Y1 - Y2) / mu
         Z = zs(R)
@@ -185,7 +186,8 @@ def lrr_alm(C: np.ndarray, M: np.ndarray, lam: float, rho: float = 1.1, mu0: flo
         r1 = float(np.abs(leq1).max()) if leq1.size else 0.0
         r2 = float(np.abs(leq2).max()) if leq2.size else 0.0
         if keep_trace:
-            trace.append((mu, r1, r2, JU.shape[1]))
+            # (mu, primal residual, ||Z - J||_inf, SVT rank, ||SVT input||_F)
+            trace.append((mu, r1, r2, JU.shape[1], float(np.linalg.norm(A))))
         if fixed_iters is None and max(r1, r2) < eps:
             converged = True
             break
@@ -238,23 +240,51 @@ class DFCResult:
     blocks: list          # per-block LRRResult
 
 
+_WORKER = {}
+
+
+def _worker_init(M):
+    _WORKER["M"] = M
+    _WORKER["zs"] = ZSolve(M)
+
+
+def _worker_block(args):
+    cols, lam, rho, mu0, mu_max, eps, max_iter, fi = args
+    M = _WORKER["M"]
+    return lrr_alm(M[:, cols], M, lam, rho, mu0, mu_max, eps, max_iter, fixed_iters=fi, zsolve=_WORKER["zs"])
+
+
 def dfc_lrr(M: np.ndarray, perm: np.ndarray, offsets: np.ndarray, lam: float, rho: float = 1.1,
             mu0: float = 1e-6, mu_max: float = 1e10, eps: float = 1e-6, max_iter: int = 1000,
-            fixed_iters=None, blocks_only=None) -> DFCResult:
+            fixed_iters=None, blocks_only=None, workers: int = 0) -> DFCResult:
     """Algorithm 1.  ``perm``/``offsets`` are the D step's random draw: block i
     observes the original columns perm[offsets[i]:offsets[i+1]].  ``fixed_iters``
     may be an int or a per-block sequence.  ``blocks_only`` restricts the F
-    step to the listed block indices (then no C step is taken)."""
+    step to the listed block indices (then no C step is taken).  With
+    ``workers`` > 1 the independent block problems of the F step ("do in
+    parallel") run in that many spawned processes; the arithmetic is the same."""
     M = np.asarray(M, dtype=np.float64)
     m, n = M.shape
     t = len(offsets) - 1
-    zs = ZSolve(M)
-    which = range(t) if blocks_only is None else blocks_only
+    which = list(range(t) if blocks_only is None else blocks_only)
+
+    def fixed(i):
+        return fixed_iters[i] if isinstance(fixed_iters, (list, tuple, np.ndarray)) else fixed_iters
+
     res = {}
-    for i in which:
-        cols = perm[offsets[i]:offsets[i + 1]]
-        fi = fixed_iters[i] if isinstance(fixed_iters, (list, tuple, np.ndarray)) else fixed_iters
-        res[i] = lrr_alm(M[:, cols], M, lam, rho, mu0, mu_max, eps, max_iter, fixed_iters=fi, zsolve=zs)
+    if workers > 1 and len(which) > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        jobs = [(perm[offsets[i]:offsets[i + 1]], lam, rho, mu0, mu_max, eps, max_iter, fixed(i)) for i in which]
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"),
+                                 initializer=_worker_init, initargs=(M,)) as ex:
+            for i, r in zip(which, ex.map(_worker_block, jobs)):
+                res[i] = r
+    else:
+        zs = ZSolve(M)
+        for i in which:
+            cols = perm[offsets[i]:offsets[i + 1]]
+            res[i] = lrr_alm(M[:, cols], M, lam, rho, mu0, mu_max, eps, max_iter, fixed_iters=fixed(i), zsolve=zs)
     iters = np.array([res[i].iters if i in res else 0 for i in range(t)], dtype=np.int64)
     resid = np.array([[res[i].resid_primal, res[i].resid_zj] if i in res else [0.0, 0.0]
                       for i in range(t)])

@@ -261,3 +261,127 @@ def test_planted_mistakes_are_caught(monkeypatch):
     assert not _pins_hold()
     monkeypatch.setattr(lrr, "ZSolve", orig_zs)
     assert _pins_hold()
+
+
+# --------------------------------------------- the DFC driver with t > 1 blocks
+
+def _subspace_projectors(d):
+    """Per subspace k, the n x n projector P_k onto the row space of that
+    subspace's columns (zero outside its own rows and columns).  For
+    independent subspaces the shape-interaction matrix V V^T of M is the sum
+    of the P_k (Section 2.1: block diagonal after sorting by subspace)."""
+    n = d.M.shape[1]
+    out = []
+    for k in range(d.k):
+        idx = np.flatnonzero(d.labels == k)
+        _, s, Vt = np.linalg.svd(d.M[:, idx], full_matrices=False)
+        rk = int((s > 1e-10 * s[0]).sum())
+        P = np.zeros((n, n))
+        P[np.ix_(idx, idx)] = Vt[:rk].T @ Vt[:rk]
+        out.append(P)
+    return out
+
+
+def _block_lambda(M, perm, offsets):
+    """A lam above which every clean block problem of eq. (2) has S = 0 and
+    Z_i = M^+ C_i (derived sufficient condition): with Z_i = U_z S_z V_z^T,
+    Y = (M^+)^T U_z V_z^T is a dual certificate (M^T Y = U_z V_z^T is a
+    subgradient of the nuclear norm at Z_i) whose columns must have norm
+    below lam.  Returns 1.5 times the largest such column norm."""
+    Mp = np.linalg.pinv(M, rcond=1e-10)
+    worst = 0.0
+    for i in range(len(offsets) - 1):
+        Zi = Mp @ M[:, perm[offsets[i]:offsets[i + 1]]]
+        Uz, sz, Vzt = np.linalg.svd(Zi, full_matrices=False)
+        kz = int((sz > 1e-10 * sz[0]).sum())
+        Y = Mp.T @ (Uz[:, :kz] @ Vzt[:kz])
+        worst = max(worst, float(np.linalg.norm(Y, axis=0).max()))
+    return 1.5 * worst
+
+
+def _clean_dfc_case():
+    """Clean data from 3 independent 3-dimensional subspaces of R^40, 20
+    points each, split at random into t = 3 uneven blocks that each hold at
+    least 4 points of every subspace (so every block spans the row space)."""
+    d = synth.union_of_subspaces(21, 40, 3, 3, 20, 0.0)
+    rng = np.random.default_rng(5)
+    for _ in range(1000):
+        perm = rng.permutation(60).astype(np.int64)
+        offsets = np.array([0, 17, 38, 60], dtype=np.int64)
+        ok = all(np.bincount(d.labels[perm[offsets[i]:offsets[i + 1]]], minlength=3).min() >= 4 for i in range(3))
+        if ok:
+            return d, perm, offsets
+    raise RuntimeError("no spanning partition drawn")
+
+
+def _dfc_pin_holds(d, perm, offsets, lam):
+    P = _subspace_projectors(d)
+    res = lrr.dfc_lrr(d.M, perm, offsets, lam, eps=1e-10, max_iter=3000)
+    return (res.Z.shape == (60, 60) and np.allclose(res.Z, sum(P), atol=1e-7)
+            and np.abs(res.S).max() < 1e-7 and res.k1 == 9)
+
+
+def test_dfc_on_spanning_blocks_returns_the_shape_interaction_matrix():
+    """Algorithm 1 with t = 3 on clean independent subspaces where every block
+    spans the row space of M: each block solution is M^+ C_i = V V^T[:, cols_i],
+    Z_1 spans the column space of [Z_1 .. Z_t] (Cor. 4), so the column
+    projection is exact and DFC-LRR returns V V^T = sum_k P_k with S = 0, the
+    columns back in their original order."""
+    d, perm, offsets = _clean_dfc_case()
+    lam = _block_lambda(d.M, perm, offsets)
+    assert _dfc_pin_holds(d, perm, offsets, lam)
+
+
+def test_dfc_projects_onto_block_one_when_it_misses_a_subspace():
+    """Block 1 holds points of subspaces 0 and 1 only.  Its solution's column
+    space is then range(P_0) + range(P_1), and the C step projects every
+    block's columns onto it: the estimate is P_0 + P_1 (the columns of
+    subspace 2 project to zero), with k1 = 6."""
+    d = synth.union_of_subspaces(21, 40, 3, 3, 20, 0.0)
+    rng = np.random.default_rng(6)
+    lab = d.labels
+    first = np.concatenate([rng.permutation(np.flatnonzero(lab == 0))[:7],
+                            rng.permutation(np.flatnonzero(lab == 1))[:8]])
+    rest = rng.permutation(np.setdiff1d(np.arange(60), first))
+    perm = np.concatenate([rng.permutation(first), rest]).astype(np.int64)
+    offsets = np.array([0, 15, 38, 60], dtype=np.int64)
+    lam = _block_lambda(d.M, perm, offsets)
+    P = _subspace_projectors(d)
+    res = lrr.dfc_lrr(d.M, perm, offsets, lam, eps=1e-10, max_iter=3000)
+    assert res.k1 == 6
+    assert np.allclose(res.Z, P[0] + P[1], atol=1e-7)
+    assert np.abs(res.S).max() < 1e-7
+
+
+def test_planted_dfc_driver_mistakes_are_caught(monkeypatch):
+    """Blocks concatenated out of order, or the C-step basis taken from the
+    last block instead of block 1, each break one of the two DFC pins."""
+    d, perm, offsets = _clean_dfc_case()
+    lam = _block_lambda(d.M, perm, offsets)
+    assert _dfc_pin_holds(d, perm, offsets, lam)
+    orig_proj = lrr.col_proj
+    monkeypatch.setattr(lrr, "col_proj", lambda Zb, basis: orig_proj(list(Zb)[::-1], basis))
+    assert not _dfc_pin_holds(d, perm, offsets, lam)
+    monkeypatch.setattr(lrr, "col_proj", orig_proj)
+    assert _dfc_pin_holds(d, perm, offsets, lam)
+
+    # basis from the last block: invisible when every block spans, caught by
+    # the pin whose block 1 misses a subspace
+    seen = []
+    orig_alm, orig_orth = lrr.lrr_alm, lrr.orth_basis
+
+    def recording_alm(*a, **k):
+        r = orig_alm(*a, **k)
+        seen.append(r)
+        return r
+
+    def last_block_basis(U, drop_tol=1e-10):
+        return orig_orth(seen[-1].J_U if seen else U, drop_tol)
+
+    monkeypatch.setattr(lrr, "lrr_alm", recording_alm)
+    monkeypatch.setattr(lrr, "orth_basis", last_block_basis)
+    with pytest.raises(AssertionError):
+        test_dfc_projects_onto_block_one_when_it_misses_a_subspace()
+    monkeypatch.setattr(lrr, "orth_basis", orig_orth)
+    monkeypatch.setattr(lrr, "lrr_alm", orig_alm)
+    test_dfc_projects_onto_block_one_when_it_misses_a_subspace()

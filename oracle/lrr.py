@@ -304,3 +304,57 @@ def dfc_lrr(M: np.ndarray, perm: np.ndarray, offsets: np.ndarray, lam: float, rh
     Z[:, perm] = Zc
     S[:, perm] = Ec
     return DFCResult(Z=Z, S=S, iters=iters, resid=resid, k1=k1, blocks=blocks)
+
+
+# --------------------------------------------------------------------------
+# Footnote variant of the F and C steps (Section 2.2, footnote to eq. (2))
+# --------------------------------------------------------------------------
+
+def lowrank_blockdiag(Z_blocks: list, k: int):
+    """Best rank-k approximation (truncated SVD) of the block-diagonal matrix
+    diag(Z_1, ..., Z_t).  Its singular triplets are the union of the blocks'
+    triplets, so the k largest singular values over all blocks are kept, each
+    block keeping its own.  Ties are broken by block order, then by position.
+    Returns the list of truncated blocks."""
+    svds = [np.linalg.svd(Zb, full_matrices=False) for Zb in Z_blocks]
+    allv = [(-s[j], b, j) for b, (_, s, _) in enumerate(svds) for j in range(len(s))]
+    allv.sort()
+    keep = {(b, j) for _, b, j in allv[:max(0, int(k))]}
+    out = []
+    for b, (U, s, Vt) in enumerate(svds):
+        idx = [j for j in range(len(s)) if (b, j) in keep]
+        out.append((U[:, idx] * s[idx]) @ Vt[idx] if idx else np.zeros_like(Z_blocks[b]))
+    return out
+
+
+def dfc_lrr_local(M: np.ndarray, perm: np.ndarray, offsets: np.ndarray, lam: float, rho: float = 1.1,
+                  mu0: float = 1e-6, mu_max: float = 1e10, eps: float = 1e-6, max_iter: int = 1000,
+                  fixed_iters=None, k=None) -> DFCResult:
+    """The alternative formulation of the footnote to eq. (2): both instances
+    of M in the block problem become C_i,
+        min ||Z_i||_* + lam ||S_i||_{2,1}  s.t.  C_i = C_i Z_i + S_i   (Z_i: l_i x l_i),
+    and the C step is a low-rank approximation of diag(Z_1, ..., Z_t), here
+    the truncated SVD at rank k (reading: the footnote leaves the rank open;
+    by default k = k1, the SVT rank of block 1 at its final iteration, the
+    same rank the column projection keeps).  Z is n x n with block i's
+    rows and columns at the original columns perm[offsets[i]:offsets[i+1]]."""
+    M = np.asarray(M, dtype=np.float64)
+    m, n = M.shape
+    t = len(offsets) - 1
+    blocks = []
+    for i in range(t):
+        cols = perm[offsets[i]:offsets[i + 1]]
+        C = M[:, cols]
+        fi = fixed_iters[i] if isinstance(fixed_iters, (list, tuple, np.ndarray)) else fixed_iters
+        blocks.append(lrr_alm(C, C, lam, rho, mu0, mu_max, eps, max_iter, fixed_iters=fi))
+    k1 = blocks[0].rank if k is None else int(k)
+    approx = lowrank_blockdiag([b.Z for b in blocks], k1)
+    Z = np.zeros((n, n))
+    S = np.empty((m, n))
+    for i in range(t):
+        cols = perm[offsets[i]:offsets[i + 1]]
+        Z[np.ix_(cols, cols)] = approx[i]
+        S[:, cols] = blocks[i].E
+    iters = np.array([b.iters for b in blocks], dtype=np.int64)
+    resid = np.array([[b.resid_primal, b.resid_zj] for b in blocks])
+    return DFCResult(Z=Z, S=S, iters=iters, resid=resid, k1=k1, blocks=blocks)

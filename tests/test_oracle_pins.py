@@ -385,3 +385,72 @@ def test_planted_dfc_driver_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(lrr, "orth_basis", orig_orth)
     monkeypatch.setattr(lrr, "lrr_alm", orig_alm)
     test_dfc_projects_onto_block_one_when_it_misses_a_subspace()
+
+
+# ------------------------------------------ footnote variant (dictionary C_i)
+
+def test_lowrank_blockdiag_keeps_the_global_top_k():
+    """The truncated SVD of a block-diagonal matrix, from blocks with known
+    singular values: the k largest over all blocks survive."""
+    rng = np.random.default_rng(12)
+    specs = [np.array([5.0, 1.0, 0.2]), np.array([3.0, 2.5]), np.array([4.0, 0.1, 0.05, 0.01])]
+    blocks = []
+    for sv in specs:
+        l = len(sv) + 2
+        U = np.linalg.qr(rng.standard_normal((l, len(sv))))[0]
+        V = np.linalg.qr(rng.standard_normal((l, len(sv))))[0]
+        blocks.append((U * sv) @ V.T)
+    out = lrr.lowrank_blockdiag(blocks, 4)        # keeps 5, 4, 3, 2.5
+    got = [np.linalg.svd(o, compute_uv=False) for o in out]
+    assert np.allclose(got[0][:2], [5.0, 0.0], atol=1e-12)
+    assert np.allclose(got[1][:2], [3.0, 2.5], atol=1e-12)
+    assert np.allclose(got[2][:2], [4.0, 0.0], atol=1e-12)
+    # the kept parts are the blocks' own leading triplets
+    U, s, Vt = np.linalg.svd(blocks[0])
+    assert np.allclose(out[0], s[0] * np.outer(U[:, 0], Vt[0]), atol=1e-12)
+
+
+def test_footnote_variant_on_clean_blocks_gives_each_blocks_shape_interaction():
+    """Clean independent subspaces, every block holding enough points of each:
+    with dictionary C_i the block solution is the shape-interaction matrix of
+    C_i itself (Section 2.1), V_i V_i^T of C_i's row space; at full rank
+    (k = sum of the block ranks) the block-diagonal approximation is exact, so
+    the estimate is diag(V_i V_i^T) in the original order, and S = 0."""
+    d, perm, offsets = _clean_dfc_case()
+    t = len(offsets) - 1
+    lam = 0.0
+    ranks = []
+    expect = np.zeros((60, 60))
+    for i in range(t):
+        cols = perm[offsets[i]:offsets[i + 1]]
+        C = d.M[:, cols]
+        U, s, Vt = np.linalg.svd(C, full_matrices=False)
+        rk = int((s > 1e-10 * s[0]).sum())
+        ranks.append(rk)
+        expect[np.ix_(cols, cols)] = Vt[:rk].T @ Vt[:rk]
+        Cp = np.linalg.pinv(C, rcond=1e-10)
+        Zi = Cp @ C
+        Uz, sz, Vzt = np.linalg.svd(Zi)
+        kz = int((sz > 1e-10).sum())
+        lam = max(lam, 1.5 * np.linalg.norm(Cp.T @ (Uz[:, :kz] @ Vzt[:kz]), axis=0).max())
+    res = lrr.dfc_lrr_local(d.M, perm, offsets, lam, eps=1e-10, max_iter=3000, k=sum(ranks))
+    assert np.allclose(res.Z, expect, atol=1e-7)
+    assert np.abs(res.S).max() < 1e-7
+    # the default rank is block 1's SVT rank; the approximation has that rank
+    # and singular values 1 (every block's are)
+    res1 = lrr.dfc_lrr_local(d.M, perm, offsets, lam, eps=1e-10, max_iter=3000)
+    assert res1.k1 == ranks[0]
+    sv = np.linalg.svd(res1.Z, compute_uv=False)
+    assert np.allclose(sv[:ranks[0]], 1.0, atol=1e-7) and sv[ranks[0]] < 1e-7
+
+
+def test_footnote_variant_with_one_block_is_lrr_truncated():
+    w = synth.workload("tiny_20x30")
+    M = w.M
+    n = M.shape[1]
+    perm = np.arange(n)
+    res = lrr.dfc_lrr_local(M, perm, np.array([0, n]), w.lam, eps=1e-8)
+    ref = lrr.lrr_alm(M, M, w.lam, eps=1e-8)
+    U, s, Vt = np.linalg.svd(ref.Z)
+    k = ref.rank
+    assert np.allclose(res.Z, (U[:, :k] * s[:k]) @ Vt[:k], atol=1e-10)

@@ -115,19 +115,23 @@ def algorithmic_work(w, rank_M, iters):
     return _elementwise(out, w, r, m, l, it, fb)
 
 
-def jacobi_work(w, rank_M, sweeps_total):
-    """Algorithmic flops of the one-sided block-Jacobi sweeps: per sweep and
-    block, the pivot Grams cost 4 L p^2 and the rotations of X and W
-    4 (L + p) p^2 (round-robin pairing of p/b blocks of width b: every round
-    forms and applies p/(2b) Grams of width 2b), i.e. 8 L p^2 + 4 p^3 with
-    L = rank(M), p = l for a tall block and L = l, p = rank(M) for a wide one.
-    The sweeps are spread evenly over the blocks."""
+def jacobi_work(w, rank_M, sweeps):
+    """Flops of the Jacobi sweeps, given the per-block sweep counts.
+
+    Returns (method, implementation):
+      method          4 p^3 per block-sweep: the eigensolve of the p x p Gram
+                      of the SVT input, one cyclic sweep (p = min(rank(M), l));
+      implementation  8 L p^2 + 4 p^3 per block-sweep: what the one-sided
+                      block Jacobi executes (every pivot Gram formed afresh
+                      from the L-long columns, 4 L p^2 over a sweep, plus the
+                      rotations of X and W, 4 (L + p) p^2), L = rank(M) for a
+                      tall block and L = l for a wide one."""
     r = rank_M
     l = np.diff(w.offsets).astype(np.float64)
     L = np.where(l <= r, r, l)
     p = np.where(l <= r, l, r)
-    per_sweep = 8 * L * p * p + 4 * p ** 3
-    return float(sweeps_total / len(l) * per_sweep.sum())
+    sw = np.asarray(sweeps, dtype=np.float64)
+    return float(np.sum(sw * 4 * p ** 3)), float(np.sum(sw * (8 * L * p * p + 4 * p ** 3)))
 
 
 def _elementwise(out, w, r, m, l, it, fb):
@@ -164,7 +168,8 @@ def bench_ours(args, rank, world):
     Mh = np.asfortranarray(w.M.astype(dt))
     Md = torch.from_numpy(Mh).to(dev)
     opts = binding.options(w.lam, rho=w.rho, mu0=w.mu0, mu_max=w.mu_max, eps=w.eps, max_iter=w.max_iter,
-                           precision=args.precision, batched=not args.sequential, profile=True)
+                           precision=args.precision, batched=not args.sequential, profile=True,
+                           autotune=not args.no_autotune)
     ws = torch.empty(binding.workspace_bytes(binding.column_major(Md), w.perm, w.offsets, opts), dtype=torch.uint8,
                      device=dev)
 
@@ -230,8 +235,8 @@ def bench_ours(args, rank, world):
     # ---- roofline of the dominant kernel family
     peaks, src = _peaks()
     work = algorithmic_work(w, res.rank_M, res.iters)
-    sweeps = float(np.mean([r_.stats["svt_sweeps"] for r_ in results]))
-    work["jacobi"] = {"flops": jacobi_work(w, res.rank_M, sweeps), "bytes": None}
+    jm, ji = jacobi_work(w, res.rank_M, res.sweeps)
+    work["jacobi"] = {"flops": jm, "flops_impl": ji, "bytes": None}
     loop_phases = [k for k in binding.PHASES if k not in ("setup", "combine", "host")]
     dom = max(loop_phases, key=lambda k: phase_ms[k])
     sm_max = peaks.get("sm_max_mhz", 2070.0)
@@ -249,6 +254,11 @@ def bench_ours(args, rank, world):
             roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                     "traffic": None, "kernel": dom,
                     "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz"}
+            if "flops_impl" in wk:
+                roof["count"] = "4 p^3 per block-sweep (the p x p Gram eigensolve), per-block sweep counts"
+                roof["achieved_impl"] = wk["flops_impl"] / sec / 1e12
+                roof["frac_impl"] = roof["achieved_impl"] / pk
+                roof["count_impl"] = "8 L p^2 + 4 p^3 per block-sweep (fresh pivot Grams + rotations)"
     else:
         roof = {"bound": "alu", "achieved": None, "peak": fp32_alu_peak_tflops(sm_max), "unit": "TFLOP/s",
                 "frac": None, "traffic": None, "kernel": dom,
@@ -262,6 +272,7 @@ def bench_ours(args, rank, world):
         "config": {"workload": args.workload, "m": int(m), "n": int(n), "t": int(w.t), "lambda": w.lam,
                    "eps": w.eps, "precision": args.precision, "batched": not args.sequential,
                    "rank_M": res.rank_M, "k1": res.k1, "parallelism": "replicas" if world > 1 else "single",
+                   "autotune": not args.no_autotune,
                    "l2": "no flush: the per-iteration working set (C, P, MZ, E, Y1 and the reduced state) "
                          "exceeds the 129 MB L2"},
         "alm_iters_per_s": float(np.max(res.iters)) / solve_s,
@@ -274,23 +285,28 @@ def bench_ours(args, rank, world):
         "gpu_launches": launches * args.steps,
         "clocks": clk,
     }
+    line["svt"]["sweeps_per_block"] = res.sweeps.tolist()
     if not args.no_compare and not args.sequential and rank == 0:
+        if args.precision == "mixed":
+            # the same batched solve in plain float32: separates the gain of
+            # the bf16 products from that of batching
+            line["fp32_batched"] = compare_sequential(binding, w, Md, dev, stream, res, batched=True)
         line["fp32_one_block_at_a_time"] = compare_sequential(binding, w, Md, dev, stream, res)
     return line, w, res
 
 
-def compare_sequential(binding, w, Md, dev, stream, res_batched, warmup=0, steps=1):
-    """The plain float32 form solving the blocks one after another on the same
-    input: the comparison point for the batched (mixed) solve.  Returns its
-    solve time, iteration counts and the relative Frobenius difference of its
-    Z against the batched solve's Z.  One solve, not warmed up: it takes about
-    100 s at the 1000 x 20000 workload, and the kernels are already loaded by
-    the batched runs."""
+def compare_sequential(binding, w, Md, dev, stream, res_batched, warmup=0, steps=1, batched=False):
+    """The plain float32 form on the same input, solving the blocks one after
+    another (batched=False: the comparison point for the batched mixed solve)
+    or all together (batched=True).  Returns its solve time, iteration counts
+    and the relative Frobenius difference of its Z against the batched
+    solve's Z.  One solve, not warmed up (the kernels are already loaded by
+    the batched runs)."""
     import torch
     if Md.dtype != torch.float32:
         return None
     opts = binding.options(w.lam, rho=w.rho, mu0=w.mu0, mu_max=w.mu_max, eps=w.eps, max_iter=w.max_iter,
-                           precision="f32", batched=False, profile=False)
+                           precision="f32", batched=batched, profile=False)
     ws = torch.empty(binding.workspace_bytes(binding.column_major(Md), w.perm, w.offsets, opts), dtype=torch.uint8,
                      device=dev)
     for _ in range(warmup):
@@ -353,8 +369,31 @@ def extrapolate(w, per_iter_s, setup_s, iters):
     return setup_s + float(np.sum(np.asarray(iters) * per_iter_s * l / l0))
 
 
+def bench_gemm(args):
+    """The iteration's tensor-core products on their own, at the shape of U^T P
+    for the whole batch: M = rank(M), N = n, K = m (1000 x 20000 x 1000 for
+    the 1000 x 20000 workload).  Device time per launch from CUDA events
+    around `steps` back-to-back launches (lrr_gemm_timing), as a fraction of
+    the measured bf16 peak (the split-TF32 product does three TF32 MMAs per
+    term: its algorithmic rate counts the float32 product's 2 M N K flops).
+    Also the command the tensor-pipe counters are captured from."""
+    import torch
+    from paper_1304_5583_gb300 import binding
+    M, N, K = args.gemm_shape
+    torch.cuda.set_device(0)
+    peaks, src = _peaks()
+    out = {"shape": [M, N, K], "peak_source": src, "bf16_peak_tflops": peaks["bf16_tflops"]}
+    for kind in ("bf16", "3xtf32"):
+        ms = binding.gemm_timing(kind, M, N, K, repeat=max(1, args.steps))
+        tf = 2.0 * M * N * K / (ms / 1e3) / 1e12
+        out[kind] = {"ms_per_launch": ms, "tflops": tf, "frac_of_bf16_peak": tf / peaks["bf16_tflops"]}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--gemm-only", action="store_true", help="time lrr_gemm_bf16 alone (see bench_gemm)")
+    ap.add_argument("--gemm-shape", type=int, nargs=3, default=[1000, 20000, 1000])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -364,6 +403,7 @@ def main():
     ap.add_argument("--sequential", action="store_true", help="solve the blocks one at a time")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-autotune", action="store_true", help="fixed launch shapes instead of the autotuner")
     ap.add_argument("--oracle-iters", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
@@ -377,6 +417,10 @@ def main():
         w = synth.workload(args.workload, seed=args.seed)
         p_iter, s_setup, _, desc = oracle_sample(w, n_iter=args.oracle_iters)
         print(json.dumps({"per_iter": p_iter, "setup": s_setup, "desc": desc}))
+        return
+
+    if args.gemm_only:
+        bench_gemm(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

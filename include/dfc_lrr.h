@@ -93,6 +93,13 @@ typedef struct {
                                    ||Z + Y2/mu||_F > mixed_switch / mu, i.e. just before
                                    its SVT first keeps a direction (0 -> 0.5)            */
     int32_t profile;            /* 1: record per-phase CUDA-event times into stats     */
+    int32_t simt_products;      /* F32/MIXED: 1 = the float32 products of the iteration on
+                                   the CUDA cores; 0 (default) = on the tensor cores in
+                                   split TF32 (float32-accurate, see lrr_gemm_f32)      */
+    int32_t autotune;           /* 1: pick the launch shapes of the Jacobi and of the
+                                   products by timing the candidates on the first solve
+                                   of each problem shape (cached per process and device);
+                                   0: fixed defaults                                     */
 } lrr_options;
 
 /* Per-phase device time of one solve, measured with CUDA events recorded on
@@ -134,7 +141,25 @@ typedef struct {
                                    block at its final iteration]                          */
     double* timings_ms;         /* (host, may be NULL) 3: setup, iteration, combine        */
     lrr_stats* stats;           /* (host, may be NULL) per-phase times and launch counts  */
+    /* Factored form of the combined estimate (Section 2.2: the column
+     * projection is cheap because the block solutions come in factored form;
+     * Z = F G costs (n + n) k values instead of n^2):  Z = F[:, :k] G[:k, :]
+     * with F orthonormal.  kmax = lrr_factor_max_rank(p); k <= kmax is
+     * returned in *factor_k.  For t > 1, F spans the column space of Z_1 (the
+     * C step's basis, k = k1) and G = F^T [Z_1 ... Z_t]; for t = 1, F is the
+     * right singular basis V of M (k = rank(M)) and G = V^T Z. */
+    void* F;                    /* (device, may be NULL) n x kmax, ld n                   */
+    void* G;                    /* (device, may be NULL) kmax x n, ld kmax, original
+                                   column order                                          */
+    int32_t* factor_k;          /* (host, may be NULL) 1: k                               */
+    int32_t* sweeps;            /* (host, may be NULL) t: Jacobi sweeps run per block,
+                                   summed over its iterations                            */
 } lrr_result;
+
+/* Largest k the factored output (lrr_result.F / .G) can have: min(m, l_1)
+ * for t > 1 (l_1 = offsets[1], the first block's width), min(m, n) for t = 1.
+ * 0 for an invalid problem. */
+LRR_API int64_t lrr_factor_max_rank(const lrr_problem* p);
 
 /* D step of Algorithm 1 (Section 2.2), on the host: a uniformly random
  * permutation of 0..n-1 into perm (n entries, may be NULL) and the even split
@@ -160,6 +185,21 @@ LRR_API int lrr_solve(const lrr_problem* p, const lrr_options* o, void* workspac
  * where it is the identity).  Returns an lrr_status. */
 LRR_API int dfc_lrr_solve(const lrr_problem* p, const lrr_options* o, void* workspace, size_t workspace_bytes,
                   lrr_result* r, void* stream);
+
+/* The alternative formulation of the footnote to eq. (2): both instances of
+ * M become C_i, so block i solves
+ *   min ||Z_i||_* + lambda ||S_i||_{2,1}  s.t.  C_i = C_i Z_i + S_i   (Z_i: l_i x l_i),
+ * and the C step is a low-rank approximation of diag(Z_1, ..., Z_t): its
+ * truncated SVD at rank `rank` (<= 0: k1, the SVT rank of block 1 at its final
+ * iteration; the footnote leaves the rank open).  The block problems have
+ * different dictionaries and run as independent problems on `streams`
+ * concurrent streams (lrr_solve_batch).  r->Z (device, n x n, original order;
+ * zero outside the diagonal blocks) and r->S as for dfc_lrr_solve; r->F/G are
+ * not produced (LRR_ERR_UNSUPPORTED if given); r->ranks = [largest rank(C_i),
+ * rank used, SVT rank of each block].  Scratch via cudaMallocAsync.
+ * Returns an lrr_status. */
+LRR_API int dfc_lrr_solve_local(const lrr_problem* p, const lrr_options* o, int64_t rank, lrr_result* r,
+                                int32_t streams, void* stream);
 
 /* Singular-value thresholding, the proximal map of tau ||.||_* that forms the
  * J-step of every ALM iteration: for A = U diag(s) V^T,
@@ -209,6 +249,94 @@ LRR_API size_t lrr_svt_noalloc_capacity(void);
  * Scratch: one int taken with cudaMallocAsync. */
 LRR_API int lrr_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
                           int64_t N, int64_t K, void* stream);
+
+/* The float32-accurate tensor-core product of the iteration on its own:
+ * C = A B with A (M x K) and B (K x N) float32, both stored K-major (element
+ * (m, k) at A[k + m lda], element (k, n) at B[k + n ldb]); C float,
+ * column-major, ldc >= M; N <= 8388480.  Every operand is split into a TF32
+ * part and a float32 remainder and three TF32 tensor-core products are summed
+ * in float32 (error near that of a float32 product; the remainders' product,
+ * below 2^-20 |a||b| per term, is dropped).  All device pointers; scratch (the
+ * split operands, 8 (M + N) K bytes) is taken with cudaMallocAsync; the call
+ * synchronises `stream`. */
+LRR_API int lrr_gemm_f32(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
+                         int64_t N, int64_t K, void* stream);
+
+/* Device time of the iteration's tensor-core product alone, for measuring
+ * it: kind 0 = the bf16 product (lrr_gemm_bf16), kind 1 = the split-TF32
+ * product (lrr_gemm_f32) on operands already split.  Fills synthetic M x K
+ * and K x N operands in scratch taken with cudaMallocAsync, launches the
+ * kernel once untimed and `repeat` times back to back between two CUDA
+ * events on `stream`, and stores the mean time per launch (ms). */
+LRR_API int lrr_gemm_timing(int32_t kind, int64_t M, int64_t N, int64_t K, int32_t repeat, double* ms_per_launch,
+                            void* stream);
+
+/* Differentiable unrolled LRR.  The map (M, lambda) -> Z_K: plain LRR
+ * (eq. (1), t = 1, the observations are the dictionary) run for exactly K
+ * iterations of the inexact ALM the solver uses (Section 4's base solver),
+ * from the zero start, the K-th iteration without its dual step; the penalty
+ * follows the fixed schedule mu_k = min(rho^(k-1) mu0, mu_max).
+ * lrr_unrolled_backward returns the gradients of a loss L(Z_K) given
+ * Zbar = dL/dZ_K: dL/dM (both the dictionary's and the observations' part)
+ * and dL/dlambda, by a hand-written reverse pass (the SVT derivative through
+ * the singular triplets, the column-shrink Jacobian, the Z-update solve, the
+ * dual steps) that recomputes the iterates from states kept every
+ * `checkpoint` iterations. */
+typedef struct {
+    double lambda;          /* > 0                                                    */
+    double rho;             /* >= 1                                                   */
+    double mu0;             /* > 0                                                    */
+    double mu_max;          /* >= mu0                                                 */
+    double rank_tol;        /* rank(M) threshold relative to sigma_max (0 -> 1e-6)    */
+    int32_t K;              /* iterations, >= 1                                       */
+    int32_t checkpoint;     /* iterations between kept states (0 -> 5)                */
+    int32_t precision;      /* LRR_PREC_F32 or LRR_PREC_F64                           */
+} lrr_unrolled_options;
+
+/* Device workspace for a forward (with_grad = 0) or backward (with_grad = 1)
+ * call of an m x n problem (0 on invalid arguments); m <= 4096, n <= 16384. */
+LRR_API size_t lrr_unrolled_workspace_bytes(int64_t m, int64_t n, const lrr_unrolled_options* o, int32_t with_grad);
+
+/* Z (device, n x n, ld ldz >= n) = Z_K(M, lambda).  M (device) m x n, ld ldm,
+ * float or double as o->precision.  workspace NULL: cudaMallocAsync on
+ * stream.  Synchronises stream.  Returns an lrr_status. */
+LRR_API int lrr_unrolled_forward(const void* M, int64_t m, int64_t n, int64_t ldm, const lrr_unrolled_options* o,
+                                 void* Z, int64_t ldz, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Mbar (device, m x n, ld ldmb) = dL/dM and *lambar (host) = dL/dlambda for
+ * Zbar = dL/dZ_K (device, n x n, ld ldzb).  Synchronises stream. */
+LRR_API int lrr_unrolled_backward(const void* M, int64_t m, int64_t n, int64_t ldm, const lrr_unrolled_options* o,
+                                  const void* Zbar, int64_t ldzb, void* Mbar, int64_t ldmb, double* lambar,
+                                  void* workspace, size_t workspace_bytes, void* stream);
+
+/* Segmentation of an estimate Z (Section 4.1.2's post-processing), on the
+ * GPU, from its factored form Z = F[:, :k] G[:k, :] (lrr_result.F / .G):
+ * U = the left singular vectors of Z with singular value > rel_tol * s_max
+ * (the paper's "top" singular vectors; reading: rel_tol = 1e-6), affinity
+ * |U U^T|, the `clusters` leading eigenvectors of the normalised affinity
+ * D^-1/2 |U U^T| D^-1/2 (the smallest of the normalised Laplacian; subspace
+ * iteration, power_iters steps), rows scaled to unit norm, then k-means
+ * (k-means++ seeding from SplitMix64 of seed, `restarts` restarts, the lowest
+ * cost wins).  F (device, n x k, ld ldf), G (device, k x n, ld ldg) float;
+ * labels (host, n) receives cluster indices 0..clusters-1.  The n x n
+ * affinity lives in the workspace (lrr_segment_workspace_bytes; NULL:
+ * cudaMallocAsync).  clusters <= 64.  Synchronises stream. */
+LRR_API size_t lrr_segment_workspace_bytes(int64_t n, int64_t k, int32_t clusters, int32_t restarts);
+LRR_API int lrr_segment(const float* F, int64_t ldf, const float* G, int64_t ldg, int64_t n, int64_t k,
+                        int32_t clusters, double rel_tol, uint64_t seed, int32_t restarts, int32_t power_iters,
+                        int32_t* labels, void* workspace, size_t workspace_bytes, void* stream);
+
+/* `count` independent problems (each its own M, sizes and partition) solved
+ * with dfc_lrr_solve under the same options, concurrently: `streams` host
+ * threads (0 -> 8) each drive their own CUDA stream and take the next problem
+ * when one is done; every problem's scratch is stream-ordered on its stream
+ * (so the options' workspace is not used).  The call first synchronises
+ * `stream` (inputs ready), returns after every problem is solved, writes each
+ * problem's status into status[i] (host, may be NULL) and returns the worst
+ * (a failure before LRR_NOT_CONVERGED before LRR_OK).  results (host, count
+ * entries, may be NULL) as for dfc_lrr_solve. */
+LRR_API int lrr_solve_batch(const lrr_problem* problems, int32_t count, const lrr_options* o, lrr_result* results,
+                            int32_t* status, int32_t streams, void* stream);
 
 /* Fill `o` with the defaults above (lambda = 0.1). */
 LRR_API void lrr_default_options(lrr_options* o);

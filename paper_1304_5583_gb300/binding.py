@@ -22,7 +22,10 @@ PRECISIONS = {"f64": LRR_PREC_F64, "f32": LRR_PREC_F32, "mixed": LRR_PREC_MIXED}
 
 # every symbol include/dfc_lrr.h declares
 EXPORTS = ("dfc_partition", "lrr_workspace_bytes", "lrr_solve", "dfc_lrr_solve", "lrr_svt", "lrr_svt_noalloc",
-           "lrr_svt_noalloc_capacity", "lrr_gemm_bf16", "lrr_default_options", "lrr_status_string")
+           "lrr_svt_noalloc_capacity", "lrr_gemm_bf16", "lrr_default_options", "lrr_status_string",
+           "lrr_factor_max_rank", "lrr_gemm_f32", "lrr_unrolled_workspace_bytes", "lrr_unrolled_forward",
+           "lrr_unrolled_backward", "lrr_gemm_timing", "lrr_segment_workspace_bytes", "lrr_segment",
+           "lrr_solve_batch", "dfc_lrr_solve_local")
 
 
 class LrrProblem(ctypes.Structure):
@@ -35,11 +38,18 @@ class LrrOptions(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("rho", ctypes.c_double), ("mu0", ctypes.c_double),
                 ("mu_max", ctypes.c_double), ("eps", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("batched", ctypes.c_int32), ("jacobi_sweeps", ctypes.c_int32),
-                ("rank_tol", ctypes.c_double), ("mixed_switch", ctypes.c_double), ("profile", ctypes.c_int32)]
+                ("rank_tol", ctypes.c_double), ("mixed_switch", ctypes.c_double), ("profile", ctypes.c_int32),
+                ("simt_products", ctypes.c_int32), ("autotune", ctypes.c_int32)]
 
 NPHASE = 12
 PHASES = ("setup", "gram", "warm", "jacobi", "svt_apply", "zgemm", "zupdate", "mzgemm", "eupdate", "stop",
           "combine", "host")
+
+
+class LrrUnrolledOptions(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("rho", ctypes.c_double), ("mu0", ctypes.c_double),
+                ("mu_max", ctypes.c_double), ("rank_tol", ctypes.c_double), ("K", ctypes.c_int32),
+                ("checkpoint", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 class LrrStats(ctypes.Structure):
@@ -51,7 +61,9 @@ class LrrStats(ctypes.Structure):
 class LrrResult(ctypes.Structure):
     _fields_ = [("Z", ctypes.c_void_p), ("S", ctypes.c_void_p), ("iters", ctypes.POINTER(ctypes.c_int32)),
                 ("resid", ctypes.POINTER(ctypes.c_double)), ("ranks", ctypes.POINTER(ctypes.c_int32)),
-                ("timings_ms", ctypes.POINTER(ctypes.c_double)), ("stats", ctypes.POINTER(LrrStats))]
+                ("timings_ms", ctypes.POINTER(ctypes.c_double)), ("stats", ctypes.POINTER(LrrStats)),
+                ("F", ctypes.c_void_p), ("G", ctypes.c_void_p), ("factor_k", ctypes.POINTER(ctypes.c_int32)),
+                ("sweeps", ctypes.POINTER(ctypes.c_int32))]
 
 
 _LIB = None
@@ -85,6 +97,39 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lrr_gemm_bf16.restype = ctypes.c_int
     lib.lrr_gemm_bf16.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                   ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
+    lib.lrr_gemm_f32.restype = ctypes.c_int
+    lib.lrr_gemm_f32.argtypes = lib.lrr_gemm_bf16.argtypes
+    lib.lrr_unrolled_workspace_bytes.restype = ctypes.c_size_t
+    lib.lrr_unrolled_workspace_bytes.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(LrrUnrolledOptions),
+                                                 ctypes.c_int32]
+    lib.lrr_unrolled_forward.restype = ctypes.c_int
+    lib.lrr_unrolled_forward.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.POINTER(LrrUnrolledOptions), ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    lib.lrr_unrolled_backward.restype = ctypes.c_int
+    lib.lrr_unrolled_backward.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.POINTER(LrrUnrolledOptions), ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    lib.lrr_gemm_timing.restype = ctypes.c_int
+    lib.lrr_gemm_timing.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    lib.lrr_segment_workspace_bytes.restype = ctypes.c_size_t
+    lib.lrr_segment_workspace_bytes.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]
+    lib.lrr_segment.restype = ctypes.c_int
+    lib.lrr_segment.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, ctypes.c_int32,
+                                ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_size_t,
+                                ctypes.c_void_p]
+    lib.lrr_solve_batch.restype = ctypes.c_int
+    lib.lrr_solve_batch.argtypes = [ctypes.POINTER(LrrProblem), ctypes.c_int32, ctypes.POINTER(LrrOptions),
+                                    ctypes.POINTER(LrrResult), ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                    ctypes.c_void_p]
+    lib.dfc_lrr_solve_local.restype = ctypes.c_int
+    lib.dfc_lrr_solve_local.argtypes = [ctypes.POINTER(LrrProblem), ctypes.POINTER(LrrOptions), ctypes.c_int64,
+                                        ctypes.POINTER(LrrResult), ctypes.c_int32, ctypes.c_void_p]
+    lib.lrr_factor_max_rank.restype = ctypes.c_int64
+    lib.lrr_factor_max_rank.argtypes = [ctypes.POINTER(LrrProblem)]
     lib.lrr_default_options.restype = None
     lib.lrr_default_options.argtypes = [ctypes.POINTER(LrrOptions)]
     lib.lrr_status_string.restype = ctypes.c_char_p
@@ -115,6 +160,10 @@ class SolveResult:
     timings_ms: np.ndarray
     status: int
     stats: dict
+    F: object = None         # torch (n, kmax) or None: Z = F[:, :factor_k] @ G[:factor_k]
+    G: object = None         # torch (kmax, n) or None
+    factor_k: int = 0
+    sweeps: np.ndarray = None   # (t,) Jacobi sweeps per block
 
 
 def column_major(x):
@@ -132,13 +181,15 @@ def leading_dim(x):
 
 def options(lam: float, rho: float = 1.1, mu0: float = 1e-6, mu_max: float = 1e10, eps: float = 1e-6,
             max_iter: int = 1000, precision: str = "f32", batched: bool = True, jacobi_sweeps: int = 0,
-            rank_tol: float = 0.0, mixed_switch: float = 0.0, profile: bool = False) -> LrrOptions:
+            rank_tol: float = 0.0, mixed_switch: float = 0.0, profile: bool = False, simt_products: bool = False,
+            autotune: bool = False) -> LrrOptions:
     o = LrrOptions()
     load().lrr_default_options(ctypes.byref(o))
     o.lambda_, o.rho, o.mu0, o.mu_max, o.eps = lam, rho, mu0, mu_max, eps
     o.max_iter, o.precision, o.batched = int(max_iter), PRECISIONS[precision], int(bool(batched))
     o.jacobi_sweeps, o.rank_tol, o.mixed_switch = int(jacobi_sweeps), float(rank_tol), float(mixed_switch)
     o.profile = int(bool(profile))
+    o.simt_products, o.autotune = int(bool(simt_products)), int(bool(autotune))
     return o
 
 
@@ -183,8 +234,13 @@ def workspace_bytes(M, perm, offsets, opts: LrrOptions, t=None, seed=0) -> int:
     return int(load().lrr_workspace_bytes(ctypes.byref(p), ctypes.byref(opts)))
 
 
+def factor_max_rank(M, perm, offsets, t=None, seed=0) -> int:
+    p, keep = _problem(M, perm, offsets, t, seed)
+    return int(load().lrr_factor_max_rank(ctypes.byref(p)))
+
+
 def _solve(entry: str, M, perm, offsets, opts: LrrOptions, want_Z=True, want_S=True, workspace=None,
-           raise_on_error=True, t=None, seed=0) -> SolveResult:
+           raise_on_error=True, t=None, seed=0, want_factors=False) -> SolveResult:
     import torch
     lib = load()
     if not M.is_cuda:
@@ -203,6 +259,11 @@ def _solve(entry: str, M, perm, offsets, opts: LrrOptions, want_Z=True, want_S=T
         workspace = torch.empty(need, dtype=torch.uint8, device=M.device)
     Z = torch.empty((n, n), dtype=M.dtype, device=M.device).t() if want_Z else None
     S = torch.empty((n, m), dtype=M.dtype, device=M.device).t() if want_S else None
+    kmax = int(lib.lrr_factor_max_rank(ctypes.byref(p))) if want_factors else 0
+    F = torch.empty((kmax, n), dtype=M.dtype, device=M.device).t() if want_factors else None
+    G = torch.empty((n, kmax), dtype=M.dtype, device=M.device).t() if want_factors else None
+    fk = ctypes.c_int32(0)
+    sweeps = np.zeros(t, np.int32)
     iters = np.zeros(t, np.int32)
     resid = np.zeros((t, 2), np.float64)
     ranks = np.zeros(t + 2, np.int32)
@@ -216,6 +277,10 @@ def _solve(entry: str, M, perm, offsets, opts: LrrOptions, want_Z=True, want_S=T
     r.timings_ms = tim.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     st = LrrStats()
     r.stats = ctypes.pointer(st)
+    r.F = ctypes.c_void_p(F.data_ptr()) if F is not None else None
+    r.G = ctypes.c_void_p(G.data_ptr()) if G is not None else None
+    r.factor_k = ctypes.pointer(fk)
+    r.sweeps = sweeps.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     stream = torch.cuda.current_stream(M.device).cuda_stream
     code = getattr(lib, entry)(ctypes.byref(p), ctypes.byref(opts), ctypes.c_void_p(workspace.data_ptr()),
                                ctypes.c_size_t(workspace.numel()), ctypes.byref(r), ctypes.c_void_p(stream))
@@ -226,7 +291,8 @@ def _solve(entry: str, M, perm, offsets, opts: LrrOptions, want_Z=True, want_S=T
                        stats={"phase_ms": dict(zip(PHASES, list(st.phase_ms))),
                               "phase_launches": dict(zip(PHASES, list(st.phase_launches))),
                               "launches": int(st.launches), "iterations": int(st.iterations),
-                              "svt_sweeps": int(st.svt_sweeps), "svt_calls": int(st.svt_calls)})
+                              "svt_sweeps": int(st.svt_sweeps), "svt_calls": int(st.svt_calls)},
+                       F=F, G=G, factor_k=int(fk.value), sweeps=sweeps)
 
 
 def dfc_lrr_solve(M, perm, offsets, opts: LrrOptions, **kw) -> SolveResult:
@@ -273,3 +339,188 @@ def gemm_bf16(A_km, B_km, M: int, N: int, K: int):
     if code < 0:
         raise LrrError(code)
     return C
+
+
+def gemm_f32(A_km, B_km, M: int, N: int, K: int):
+    """C = A B on the tensor cores in split TF32 through the C ABI.  A_km:
+    float32 tensor of shape (M, lda) holding A K-major; B_km: float32 (N, ldb)
+    holding B K-major.  Returns C as a float32 (M, N) column-major tensor."""
+    import torch
+    lib = load()
+    C = torch.empty((N, M), dtype=torch.float32, device=A_km.device).t()
+    code = lib.lrr_gemm_f32(ctypes.c_void_p(A_km.data_ptr()), A_km.stride(0), ctypes.c_void_p(B_km.data_ptr()),
+                            B_km.stride(0), ctypes.c_void_p(C.data_ptr()), C.stride(1), M, N, K,
+                            ctypes.c_void_p(torch.cuda.current_stream(A_km.device).cuda_stream))
+    if code < 0:
+        raise LrrError(code)
+    return C
+
+
+def unrolled_options(lam: float, K: int, mu0: float = 1e-6, rho: float = 1.1, mu_max: float = 1e10,
+                     checkpoint: int = 5, precision: str = "f32", rank_tol: float = 0.0) -> LrrUnrolledOptions:
+    o = LrrUnrolledOptions()
+    o.lambda_, o.rho, o.mu0, o.mu_max, o.rank_tol = float(lam), float(rho), float(mu0), float(mu_max), rank_tol
+    o.K, o.checkpoint, o.precision = int(K), int(checkpoint), PRECISIONS[precision]
+    return o
+
+
+def unrolled_forward(M, opts: LrrUnrolledOptions):
+    """Z_K (n x n, column-major) of K unrolled ALM iterations through the C ABI."""
+    import torch
+    lib = load()
+    M = column_major(M)
+    m, n = M.shape
+    Z = torch.empty((n, n), dtype=M.dtype, device=M.device).t()
+    code = lib.lrr_unrolled_forward(ctypes.c_void_p(M.data_ptr()), m, n, leading_dim(M), ctypes.byref(opts),
+                                    ctypes.c_void_p(Z.data_ptr()), n, None, 0,
+                                    ctypes.c_void_p(torch.cuda.current_stream(M.device).cuda_stream))
+    if code < 0:
+        raise LrrError(code)
+    return Z
+
+
+def unrolled_backward(M, opts: LrrUnrolledOptions, Zbar):
+    """(dL/dM, dL/dlambda) for Zbar = dL/dZ_K through the C ABI."""
+    import torch
+    lib = load()
+    M = column_major(M)
+    Zbar = column_major(Zbar.to(M.dtype))
+    m, n = M.shape
+    Mb = torch.empty((n, m), dtype=M.dtype, device=M.device).t()
+    lb = ctypes.c_double(0.0)
+    code = lib.lrr_unrolled_backward(ctypes.c_void_p(M.data_ptr()), m, n, leading_dim(M), ctypes.byref(opts),
+                                     ctypes.c_void_p(Zbar.data_ptr()), leading_dim(Zbar),
+                                     ctypes.c_void_p(Mb.data_ptr()), m, ctypes.byref(lb), None, 0,
+                                     ctypes.c_void_p(torch.cuda.current_stream(M.device).cuda_stream))
+    if code < 0:
+        raise LrrError(code)
+    return Mb, lb.value
+
+
+def _unrolled_function():
+    import torch
+
+    class UnrolledLRR(torch.autograd.Function):
+        """Z_K(M, lambda) of K unrolled ALM iterations; backward by the
+        library's hand-written reverse pass (checkpointed recompute)."""
+
+        @staticmethod
+        def forward(ctx, M, lam, K, mu0, rho, mu_max, checkpoint):
+            prec = "f64" if M.dtype == torch.float64 else "f32"
+            opts = unrolled_options(float(lam), K, mu0=mu0, rho=rho, mu_max=mu_max, checkpoint=checkpoint,
+                                    precision=prec)
+            ctx.save_for_backward(M)
+            ctx.opts = opts
+            return unrolled_forward(M, opts)
+
+        @staticmethod
+        def backward(ctx, gZ):
+            (M,) = ctx.saved_tensors
+            Mb, lb = unrolled_backward(M, ctx.opts, gZ)
+            return Mb, torch.tensor(lb, dtype=M.dtype, device=M.device), None, None, None, None, None
+
+    return UnrolledLRR
+
+
+def unrolled_lrr(M, lam, K: int, mu0: float = 1e-6, rho: float = 1.1, mu_max: float = 1e10, checkpoint: int = 5):
+    """Differentiable Z_K(M, lam) (torch.autograd): gradients reach M and lam
+    (a 0-d tensor) through lrr_unrolled_backward."""
+    import torch
+    if not torch.is_tensor(lam):
+        lam = torch.tensor(float(lam), dtype=M.dtype, device=M.device)
+    return _unrolled_function().apply(M, lam, K, mu0, rho, mu_max, checkpoint)
+
+
+def gemm_timing(kind: str, M: int, N: int, K: int, repeat: int = 20) -> float:
+    """Mean device time (ms) of one launch of the bf16 ("bf16") or split-TF32
+    ("3xtf32") tensor-core product at M x N x K (lrr_gemm_timing)."""
+    import torch
+    ms = ctypes.c_double(0.0)
+    code = load().lrr_gemm_timing({"bf16": 0, "3xtf32": 1}[kind], M, N, K, repeat, ctypes.byref(ms),
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if code < 0:
+        raise LrrError(code)
+    return ms.value
+
+
+def segment(F, G, k: int, clusters: int, rel_tol: float = 1e-6, seed: int = 0, restarts: int = 20,
+            power_iters: int = 100):
+    """Cluster labels (numpy int32, n) of the estimate Z = F[:, :k] G[:k] on the
+    GPU (lrr_segment); F, G as returned by a solve with want_factors=True."""
+    import torch
+    lib = load()
+    F = column_major(F.float())
+    G = column_major(G.float())
+    n = F.shape[0]
+    labels = np.zeros(n, np.int32)
+    code = lib.lrr_segment(ctypes.c_void_p(F.data_ptr()), leading_dim(F), ctypes.c_void_p(G.data_ptr()),
+                           leading_dim(G), n, int(k), int(clusters), float(rel_tol), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                           int(restarts), int(power_iters), labels.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                           None, 0, ctypes.c_void_p(torch.cuda.current_stream(F.device).cuda_stream))
+    if code < 0:
+        raise LrrError(code)
+    return labels
+
+
+def dfc_lrr_solve_local(M, perm, offsets, opts: LrrOptions, rank: int = 0, streams: int = 8):
+    """The footnote variant (dictionary C_i per block, C step = truncated SVD of
+    diag(Z_1..Z_t)) through the C ABI.  Returns a SolveResult (no factors)."""
+    import torch
+    lib = load()
+    M = column_major(M)
+    m, n = M.shape
+    p, keep = _problem(M, perm, offsets)
+    t = p.t
+    Z = torch.empty((n, n), dtype=M.dtype, device=M.device).t()
+    S = torch.empty((n, m), dtype=M.dtype, device=M.device).t()
+    iters = np.zeros(t, np.int32)
+    resid = np.zeros((t, 2), np.float64)
+    ranks = np.zeros(t + 2, np.int32)
+    sweeps = np.zeros(t, np.int32)
+    r = LrrResult()
+    r.Z, r.S = ctypes.c_void_p(Z.data_ptr()), ctypes.c_void_p(S.data_ptr())
+    r.iters = iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    r.resid = resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    r.ranks = ranks.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    r.sweeps = sweeps.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    code = lib.dfc_lrr_solve_local(ctypes.byref(p), ctypes.byref(opts), int(rank), ctypes.byref(r), int(streams),
+                                   ctypes.c_void_p(torch.cuda.current_stream(M.device).cuda_stream))
+    if code < 0:
+        raise LrrError(code)
+    return SolveResult(Z=Z, S=S, iters=iters, resid=resid, rank_M=int(ranks[0]), k1=int(ranks[1]),
+                       block_ranks=ranks[2:].copy(), timings_ms=np.zeros(3), status=int(code), stats={},
+                       sweeps=sweeps)
+
+
+def solve_batch(Ms, opts: LrrOptions, streams: int = 8, want_Z=True, want_S=True, parts=None):
+    """Independent problems (a list of column-major CUDA tensors, each solved
+    as plain LRR unless `parts` gives (perm, offsets) per problem) on
+    concurrent streams (lrr_solve_batch).  Returns (list of (Z, S, iters),
+    per-problem status)."""
+    import torch
+    lib = load()
+    cnt = len(Ms)
+    probs = (LrrProblem * cnt)()
+    res = (LrrResult * cnt)()
+    keep, outs = [], []
+    for i, M in enumerate(Ms):
+        M = column_major(M)
+        m, n = M.shape
+        perm, off = parts[i] if parts is not None else (np.arange(n, dtype=np.int64), np.array([0, n], np.int64))
+        p, kp = _problem(M, perm, off)
+        keep += kp + [M]
+        probs[i] = p
+        Z = torch.empty((n, n), dtype=M.dtype, device=M.device).t() if want_Z else None
+        S = torch.empty((n, m), dtype=M.dtype, device=M.device).t() if want_S else None
+        it = np.zeros(p.t, np.int32)
+        keep.append(it)
+        res[i].Z = ctypes.c_void_p(Z.data_ptr()) if Z is not None else None
+        res[i].S = ctypes.c_void_p(S.data_ptr()) if S is not None else None
+        res[i].iters = it.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        outs.append((Z, S, it))
+    st = np.zeros(cnt, np.int32)
+    code = lib.lrr_solve_batch(probs, cnt, ctypes.byref(opts), res, st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                               int(streams), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if code < 0:
+        raise LrrError(code)
+    return outs, st

@@ -56,6 +56,26 @@ __global__ void copy_convert_to_f64(const T* __restrict__ src, double* __restric
         dst[i] = (double)src[i];
 }
 
+// x[i] = a uniform value in [-0.5, 0.5) from a hash of i (synthetic input for
+// timing launch shapes; its statistics do not matter)
+template <typename T>
+__global__ void fill_hash(T* __restrict__ x, int64_t count, uint32_t seed) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t h = (uint32_t)i * 0x9E3779B1u ^ seed;
+        h ^= h >> 16; h *= 0x85EBCA6Bu; h ^= h >> 13; h *= 0xC2B2AE35u; h ^= h >> 16;
+        x[i] = (T)((double)h * (1.0 / 4294967296.0) - 0.5);
+    }
+}
+
+// bf16 bit patterns of the same hashed values
+static __global__ void fill_hash_bf16(uint16_t* __restrict__ x, int64_t count, uint32_t seed) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t h = (uint32_t)i * 0x9E3779B1u ^ seed;
+        h ^= h >> 16; h *= 0x85EBCA6Bu; h ^= h >> 13; h *= 0xC2B2AE35u; h ^= h >> 16;
+        x[i] = __bfloat16_as_ushort(__float2bfloat16((float)((double)h * (1.0 / 4294967296.0) - 0.5)));
+    }
+}
+
 // square pp x pp matrix, ld pp: real part p x p is left alone; padding gets
 // `diag` on the diagonal and zeros elsewhere.  With eye != 0 the real part is
 // set to the identity too (eigenvector matrices).
@@ -172,7 +192,8 @@ __global__ void z_update(int r, int64_t n, const int* __restrict__ colblk, const
                          const T* __restrict__ Theta, const T* __restrict__ Jt, T* __restrict__ Y2t,
                          T* __restrict__ Zt, T* __restrict__ D, T* __restrict__ A, const T* __restrict__ sig,
                          const T* __restrict__ dinv, T* __restrict__ dmax, double* __restrict__ afro,
-                         uint16_t* __restrict__ dbf, int64_t ldd) {
+                         uint16_t* __restrict__ dbf, int64_t ldd, float* __restrict__ dhi,
+                         float* __restrict__ dlo, int64_t lds) {
     const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= n) return;
@@ -193,6 +214,7 @@ __global__ void z_update(int r, int64_t n, const int* __restrict__ colblk, const
         Zt[o + i] = z;
         Tt[o + i] = dl;
         if (dbf) dbf[i + j * ldd] = __bfloat16_as_ushort(__float2bfloat16((float)dl));
+        if (dhi) split_tf32((float)dl, dhi[i + j * lds], dlo[i + j * lds]);
         D[o + i] = dd;
         Y2t[o + i] = y2n;
         A[o + i] = av;
@@ -214,7 +236,8 @@ template <typename T>
 __global__ void e_update(int64_t m, int64_t n, const int* __restrict__ colblk, const int* __restrict__ act,
                          const double* __restrict__ mu, double rho, double mu_max, double lam,
                          const T* __restrict__ Cp, const T* __restrict__ UD, T* __restrict__ Y1, T* __restrict__ E,
-                         T* __restrict__ Q, T* __restrict__ r1max, uint16_t* __restrict__ qbf, int64_t ldq) {
+                         T* __restrict__ Q, T* __restrict__ r1max, uint16_t* __restrict__ qbf, int64_t ldq,
+                         float* __restrict__ qhi, float* __restrict__ qlo, int64_t lds) {
     const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= n) return;
@@ -246,6 +269,7 @@ __global__ void e_update(int64_t m, int64_t n, const int* __restrict__ colblk, c
         const T qv = y1n * imun - e;
         Q[o + i] = qv;
         if (qbf) qbf[i + j * ldq] = __bfloat16_as_ushort(__float2bfloat16((float)qv));
+        if (qhi) split_tf32((float)qv, qhi[i + j * lds], qlo[i + j * lds]);
         amax = fmax(amax, fabs(l1));
     }
     amax = warp_max(amax);
@@ -352,7 +376,7 @@ __global__ void stop_part2(int nblk, int* __restrict__ act, int* __restrict__ it
 
 // one-time factor M M^T = W diag(lam) W^T (columns of W in `order`, the r
 // kept ones): U (float64), U diag(1/sigma) (for V = M^T U diag(1/sigma))
-__global__ void setup_factors(const double* __restrict__ W, int64_t ldw, int64_t m, int r,
+static __global__ void setup_factors(const double* __restrict__ W, int64_t ldw, int64_t m, int r,
                               const int* __restrict__ order, const double* __restrict__ lam, double* __restrict__ Ud,
                               double* __restrict__ Usd) {
     const int k = blockIdx.y;
@@ -385,6 +409,35 @@ __global__ void to_bf16_transposed(const T* __restrict__ src, int64_t ld, int64_
     for (int64_t i = blockIdx.y; i < rows; i += gridDim.y)
         for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols; j += (int64_t)gridDim.x * blockDim.x)
             dst[j + i * ldo] = __bfloat16_as_ushort(__float2bfloat16((float)src[i + j * ld]));
+}
+
+// split TF32 copy of a column-major rows x cols float32 matrix (same
+// orientation, leading dimension ldo, padding rows zero): hi + lo = src with
+// hi exact in TF32 (operands of tc_gemm_3xtf32)
+template <typename T>
+__global__ void split_tf32_km(const T* __restrict__ src, int64_t ld, int64_t rows, int64_t cols,
+                              float* __restrict__ hi, float* __restrict__ lo, int64_t ldo) {
+    for (int64_t j = blockIdx.y; j < cols; j += gridDim.y)
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ldo; i += (int64_t)gridDim.x * blockDim.x) {
+            float h = 0.f, l = 0.f;
+            if (i < rows) split_tf32((float)src[i + j * ld], h, l);
+            hi[i + j * ldo] = h;
+            lo[i + j * ldo] = l;
+        }
+}
+
+// the same for the transpose: dst(j, i) = src(i, j), dst with leading
+// dimension ldo >= cols (padding zero)
+template <typename T>
+__global__ void split_tf32_transposed(const T* __restrict__ src, int64_t ld, int64_t rows, int64_t cols,
+                                      float* __restrict__ hi, float* __restrict__ lo, int64_t ldo) {
+    for (int64_t i = blockIdx.y; i < rows; i += gridDim.y)
+        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ldo; j += (int64_t)gridDim.x * blockDim.x) {
+            float h = 0.f, l = 0.f;
+            if (j < cols) split_tf32((float)src[i + j * ld], h, l);
+            hi[j + i * ldo] = h;
+            lo[j + i * ldo] = l;
+        }
 }
 
 // Theta(k, j) = sigma_k V(perm_j, k) in the iteration precision and in float64
@@ -438,12 +491,13 @@ __global__ void row_norm_max(const T* __restrict__ V, int64_t n, int r, T* __res
     atomic_max_nonneg(out, (T)(sqrt(acc) * (1.0 + 1e-6)));
 }
 
+// dst[:, perm[j]] = src[:, j] for the m x n column-major src (ld lds) and dst (ld ldd)
 template <typename T>
 __global__ void scatter_cols(const T* __restrict__ src, int64_t m, int64_t n, const int64_t* __restrict__ perm,
-                             T* __restrict__ dst) {
+                             T* __restrict__ dst, int64_t lds, int64_t ldd) {
     for (int64_t j = blockIdx.y; j < n; j += gridDim.y)
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
-            dst[i + perm[j] * m] = src[i + j * m];
+            dst[i + perm[j] * ldd] = src[i + j * lds];
 }
 
 // C-step helpers -----------------------------------------------------------
@@ -484,7 +538,7 @@ __global__ void gather_normalise_f64(const T* __restrict__ src, int64_t ld, int6
 }
 
 // X <- 1.5 X - 0.5 Y  (Newton-Schulz step for the polar factor, Y = X X^T X)
-__global__ void ns_combine(double* __restrict__ X, const double* __restrict__ Y, int64_t count) {
+static __global__ void ns_combine(double* __restrict__ X, const double* __restrict__ Y, int64_t count) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
         X[i] = 1.5 * X[i] - 0.5 * Y[i];
 }

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <cstring>
 
 namespace lrr {
 
@@ -52,7 +53,8 @@ struct JacDesc {
 template <typename T>
 cudaError_t jacobi_sweeps(const JacDesc<T>* d_desc, int nmat, int max_pp, int sweeps, T tol, cudaStream_t s);
 // One-sided block Jacobi (osj.cu): X (L x p, ld ldx) is rotated to orthogonal
-// columns together with W (p x p, ld ldw); pp = p rounded up to 2*bs.
+// columns together with W (p x p, ld ldw); pp = p rounded up to the pivot
+// width.  off points at three slots (the per-sweep convergence maxima).
 template <typename T>
 struct OsjDesc {
     T* X;
@@ -67,11 +69,20 @@ struct OsjDesc {
     int strict;         // 1: resolve pairs straddling tau to angle tol (C-step block)
 };
 
+// One launch: every block is a thread-block cluster of `cluster` CTAs (0:
+// one per pivot of a round, up to osj_max_cluster()) that runs its sweeps
+// until converged or `sweeps` are done.
 template <typename T>
 cudaError_t osj_sweeps(const OsjDesc<T>* d_desc, int nmat, int max_pp, int sweeps, T tol, int* sweeps_run,
-                       cudaStream_t s);
+                       cudaStream_t s, int cluster = 0);
+// largest cluster size osj_sweeps uses on the current device (16 or 8)
+template <typename T>
+int osj_max_cluster();
 
 template <typename T> constexpr int jacobi_bs() { return sizeof(T) == 8 ? 16 : 32; }
+// pivot width of the one-sided Jacobi (two column blocks of 16); the column
+// count p of its matrices is padded to a multiple of it
+constexpr int osj_pivot_width() { return 32; }
 
 // D step (partition.cu, host): perm and/or offsets of dfc_partition
 void draw_partition(int64_t n, int t, uint64_t seed, int64_t* perm, int64_t* offsets);
@@ -80,6 +91,42 @@ void draw_partition(int64_t n, int t, uint64_t seed, int64_t* perm, int64_t* off
 // C (M x N, column-major, float) = A B, A and B bf16 and K-major (tc_gemm.cu).
 cudaError_t tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int M, int N,
                          int K, int* err, cudaStream_t s);
+
+// Float32-accurate product on the tensor cores (split TF32): C (M x N,
+// column-major, float) = A B from A = Ahi + Alo and B = Bhi + Blo, all four
+// float32, K-major, 16-byte aligned, lda and ldb multiples of 4, hi the TF32
+// truncation of the value and lo the float32 remainder (split_tf32 below).
+// With flag != nullptr, 128-column tiles of C whose columns all belong to
+// blocks b (colblk) with flag[b] == 0 are left untouched.
+cudaError_t tc_gemm_3xtf32(const float* Ahi, const float* Alo, int64_t lda, const float* Bhi, const float* Blo,
+                           int64_t ldb, float* C, int64_t ldc, int M, int N, int K, const int* colblk,
+                           const int* flag, int* err, cudaStream_t s);
+
+// Split of x into hi + lo for the split-TF32 product: hi = x rounded to the
+// nearest TF32 value (10 explicit mantissa bits), lo = (x - hi) rounded to
+// the nearest TF32 value.  Both are exact TF32 numbers, so the tensor cores
+// use them without further rounding; |x - hi - lo| <= 2^-22 |x|, with
+// unbiased signs (truncation would bias every product the same way).
+__host__ __device__ __forceinline__ float tf32_rn(float x) {
+    uint32_t u;
+#ifdef __CUDA_ARCH__
+    u = __float_as_uint(x);
+#else
+    memcpy(&u, &x, 4);
+#endif
+    if ((u & 0x7F800000u) != 0x7F800000u) u = (u + 0x1000u) & 0xFFFFE000u;   // finite: round half away
+    float r;
+#ifdef __CUDA_ARCH__
+    r = __uint_as_float(u);
+#else
+    memcpy(&r, &u, 4);
+#endif
+    return r;
+}
+__host__ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+    hi = tf32_rn(x);
+    lo = tf32_rn(x - hi);
+}
 
 // Reduction form of the same product: C is not stored; for every column block b
 // (colblk maps a column of C to its block) with need[b] != 0 the largest |C_ij|

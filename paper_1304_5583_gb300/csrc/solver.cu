@@ -19,7 +19,10 @@
 #include <cstring>
 #include <numeric>
 #include <type_traits>
+#include <map>
 #include <mutex>
+#include <numeric>
+#include <tuple>
 #include <vector>
 
 #include "dfc_lrr.h"
@@ -115,6 +118,10 @@ struct Buffers {
     int64_t ldm8, ldr8;
     uint16_t *Ubf, *USbf, *Pbf, *Zbf;
     int *fp32_on, *gemm32, *tc_err;
+    // float32 products on the tensor cores (split TF32): U and U^T split once,
+    // P = Y1/mu - E and Delta split by the kernels that produce them
+    int64_t m4, r4;
+    float *Uh, *Ul, *UTh, *UTl, *Ph, *Pl, *Dh, *Dl;
     // float32 iteration: bf16 V (K-major) and D for the tensor-core stage of the stop test
     uint16_t *Vbf, *Dbf;
     unsigned* bmax;
@@ -126,14 +133,15 @@ struct Buffers {
 };
 
 template <typename T>
-Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector<BlockInfo<T>>& blk, bool mixed) {
+Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector<BlockInfo<T>>& blk, bool mixed,
+                 bool tc32) {
     Buffers<T> b{};
     b.m = p->m;
     b.n = p->n;
     b.t = p->t;
     b.rmax = (int)std::min<int64_t>(p->m, p->n);
     constexpr int B2d = 2 * jacobi_bs<double>();
-    constexpr int B2 = 2 * jacobi_bs<T>();
+    constexpr int B2 = osj_pivot_width();
     b.mpp = round_up((int)p->m, B2d);
     const int64_t m = p->m, n = p->n, r = b.rmax, mpp = b.mpp;
     b.Md = need_md ? a.take<double>(m * n) : nullptr;
@@ -200,7 +208,7 @@ Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector
     b.dmax = a.take<T>(t);
     b.r2x = a.take<T>(t);
     b.jscale = a.take<T>(t);
-    b.joff = a.take<T>(t);
+    b.joff = a.take<T>(3 * (size_t)t);   // three convergence slots per block
     b.perm = a.take<int64_t>(n);
     b.gd = a.take<GemmDesc<T>>(16 * (size_t)t + 16);
     b.jd = a.take<OsjDesc<T>>(t);
@@ -228,6 +236,16 @@ Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector
     b.USbf = mixed ? a.take<uint16_t>(m * b.ldr8) : nullptr;
     b.Pbf = mixed ? a.take<uint16_t>(n * b.ldm8) : nullptr;
     b.Zbf = mixed ? a.take<uint16_t>(n * b.ldr8) : nullptr;
+    b.m4 = (m + 3) / 4 * 4;
+    b.r4 = (r + 3) / 4 * 4;
+    b.Uh = tc32 ? a.take<float>(b.m4 * r) : nullptr;
+    b.Ul = tc32 ? a.take<float>(b.m4 * r) : nullptr;
+    b.UTh = tc32 ? a.take<float>(b.r4 * m) : nullptr;
+    b.UTl = tc32 ? a.take<float>(b.r4 * m) : nullptr;
+    b.Ph = tc32 ? a.take<float>(b.m4 * n) : nullptr;
+    b.Pl = tc32 ? a.take<float>(b.m4 * n) : nullptr;
+    b.Dh = tc32 ? a.take<float>(b.r4 * n) : nullptr;
+    b.Dl = tc32 ? a.take<float>(b.r4 * n) : nullptr;
     b.fp32_on = a.take<int>(t);
     b.gemm32 = a.take<int>(t);
     b.tc_err = a.take<int>(1);
@@ -244,7 +262,7 @@ Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector
 
 template <typename T>
 std::vector<BlockInfo<T>> block_info(const lrr_problem* p) {
-    constexpr int B2 = 2 * jacobi_bs<T>();
+    constexpr int B2 = osj_pivot_width();
     const int rmax = (int)std::min<int64_t>(p->m, p->n);
     std::vector<BlockInfo<T>> v((size_t)p->t);
     for (int i = 0; i < p->t; ++i) {
@@ -322,6 +340,31 @@ struct GemmSet {
     bool ta = false, tb = false;
 };
 
+// ---- autotuner: launch shape of the batched Jacobi (cluster size per block),
+// picked by timing the candidates on synthetic input of the problem's block
+// shapes the first time a shape is solved; cached per process and device.
+struct TuneKey {
+    int dev, prec;
+    int64_t m, n, r;
+    int t, max_pp;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(dev, prec, m, n, r, t, max_pp) < std::tie(o.dev, o.prec, o.m, o.n, o.r, o.t, o.max_pp);
+    }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, int> g_tune_cluster;
+
+// float32 products on the tensor cores in split TF32 (float32 iteration only;
+// the grid covers n in 128-column tiles, at most 65535 of them)
+// Jacobi sweep tolerance of the iteration (scaled off-diagonal)
+template <typename T>
+constexpr T jtol_of() { return sizeof(T) == 8 ? T(1e-13) : T(2e-6); }
+
+template <typename T>
+bool use_tc32(const lrr_problem* p, const lrr_options* o) {
+    return std::is_same<T, float>::value && o->precision != LRR_PREC_F64 && !o->simt_products && p->n <= kTcMaxN;
+}
+
 template <typename T, typename Tin>
 int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_bytes, lrr_result* res,
                cudaStream_t s, bool dfc) {
@@ -330,7 +373,8 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     Arena probe(nullptr);
     const bool mixed = o->precision == LRR_PREC_MIXED;
     if (mixed && p->n > kTcMaxN) return LRR_ERR_UNSUPPORTED;
-    carve<T>(probe, p, need_md, blk, mixed);
+    const bool tc32 = use_tc32<T>(p, o);
+    carve<T>(probe, p, need_md, blk, mixed, tc32);
     const size_t need = probe.off + kAlign;
     void* own = nullptr;
     if (!ws) {
@@ -344,7 +388,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     } guard{own, s};
     if (ws_bytes < need - kAlign || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return LRR_ERR_WORKSPACE;
     Arena arena(ws);
-    Buffers<T> B = carve<T>(arena, p, need_md, blk, mixed);
+    Buffers<T> B = carve<T>(arena, p, need_md, blk, mixed, tc32);
     const int64_t m = p->m, n = p->n;
     const int t = p->t;
     const Tin* M = static_cast<const Tin*>(p->M);
@@ -431,6 +475,16 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         k::to_bf16_transposed<T><<<dim3(grid1(B.ldr8), (unsigned)std::min<int64_t>(m, 65535)), 256, 0, s>>>(
             B.U, m, m, r, B.USbf, B.ldr8);
     }
+    if constexpr (std::is_same<T, float>::value) {
+        if (tc32) {
+            // A operands of U^T P (U itself, K = m) and of U Delta (U^T, K = r)
+            k::split_tf32_km<T><<<dim3(grid1(B.m4), (unsigned)r), 256, 0, s>>>(B.U, m, m, r, B.Uh, B.Ul, B.m4);
+            k::split_tf32_transposed<T><<<dim3(grid1(B.r4), (unsigned)std::min<int64_t>(m, 65535)), 256, 0, s>>>(
+                B.U, m, m, r, B.UTh, B.UTl, B.r4);
+            LRR_CUDA_TRY(cudaMemsetAsync(B.Ph, 0, sizeof(float) * B.m4 * n, s));
+            LRR_CUDA_TRY(cudaMemsetAsync(B.Pl, 0, sizeof(float) * B.m4 * n, s));
+        }
+    }
     hd[1] = gdesc<double>(Md, ldmd, B.Usd, m, B.Vd, n, (int)n, r, (int)m, nullptr);
     LRR_CUDA_TRY(cudaMemcpyAsync(dd + 1, &hd[1], sizeof(GemmDesc<double>), cudaMemcpyHostToDevice, s));
     LRR_CUDA_TRY(gemm_grouped<double>(dd + 1, 1, true, false, (int)n, r, s));
@@ -468,7 +522,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     }
 
     // ---- per-block tables (sizes now known: p_i = min(r, l_i))
-    constexpr int B2 = 2 * jacobi_bs<T>();
+    constexpr int B2 = osj_pivot_width();
     std::vector<int> pv((size_t)t), ppv((size_t)t);
     std::vector<char> tall((size_t)t);
     int max_p = 0, max_pp = 0, max_l = 0;
@@ -493,11 +547,60 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         j.ldx = tall[i] ? r : blk[i].l;
         j.L = tall[i] ? r : blk[i].l;
         j.W = B.W[i]; j.ldw = ppv[i]; j.p = pv[i]; j.pp = ppv[i];
-        j.done = B.jdone + i; j.off = B.joff + i; j.active = B.svt_on + i; j.scale = B.jscale + i;
+        j.done = B.jdone + i; j.off = B.joff + 3 * i; j.active = B.svt_on + i; j.scale = B.jscale + i;
         j.mu = B.mu + i;
         j.strict = (dfc && t > 1 && i == 0) ? 1 : 0;
     }
     LRR_CUDA_TRY(cudaMemcpyAsync(B.jd, jdh.data(), sizeof(OsjDesc<T>) * t, cudaMemcpyHostToDevice, s));
+
+    // ---- autotune the Jacobi's cluster size (before the state is initialised:
+    //      it runs on synthetic columns in the SVT buffers, then clears them)
+    int jcluster = 0;
+    if (o->autotune) {
+        int dev = 0;
+        LRR_CUDA_TRY(cudaGetDevice(&dev));
+        const TuneKey key{dev, o->precision, m, n, r, t, max_pp};
+        bool have = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mutex);
+            auto it = g_tune_cluster.find(key);
+            if (it != g_tune_cluster.end()) { jcluster = it->second; have = true; }
+        }
+        if (!have) {
+            std::vector<int> cand;
+            const int max_pairs = max_pp / B2, cmax = osj_max_cluster<T>();
+            for (int c : {4, 8, 16})
+                if (c <= cmax && (c <= max_pairs || cand.empty())) cand.push_back(std::min(c, max_pairs));
+            std::vector<int> on((size_t)t, 1);
+            std::vector<double> mu_t((size_t)t, 1e10);
+            LRR_CUDA_TRY(cudaMemcpyAsync(B.svt_on, on.data(), sizeof(int) * t, cudaMemcpyHostToDevice, s));
+            LRR_CUDA_TRY(cudaMemcpyAsync(B.mu, mu_t.data(), sizeof(double) * t, cudaMemcpyHostToDevice, s));
+            cudaEvent_t ta, tb;
+            LRR_CUDA_TRY(cudaEventCreate(&ta));
+            LRR_CUDA_TRY(cudaEventCreate(&tb));
+            float best = 1e30f;
+            for (int c : cand) {
+                k::fill_hash<T><<<grid1(r * n), 256, 0, s>>>(B.D, r * n, 12345u);
+                for (int i = 0; i < t; ++i)
+                    k::init_padded<T><<<grid1((int64_t)ppv[i] * ppv[i]), 256, 0, s>>>(B.W[i], pv[i], ppv[i], T(1), 1);
+                k::col_norm_max<T><<<t, 256, 0, s>>>(B.jd, B.svt_on, B.jscale, t);
+                cudaEventRecord(ta, s);
+                const cudaError_t e = osj_sweeps<T>(B.jd, t, max_pp, 2, jtol_of<T>(), nullptr, s, c);
+                cudaEventRecord(tb, s);
+                if (e != cudaSuccess || cudaEventSynchronize(tb) != cudaSuccess) {
+                    cudaEventDestroy(ta); cudaEventDestroy(tb);
+                    return LRR_ERR_CUDA;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ta, tb);
+                if (ms < best) { best = ms; jcluster = c; }
+            }
+            cudaEventDestroy(ta);
+            cudaEventDestroy(tb);
+            std::lock_guard<std::mutex> lk(g_tune_mutex);
+            g_tune_cluster[key] = jcluster;
+        }
+    }
 
     // grouped GEMM descriptor sets
     std::vector<GemmDesc<T>> gh;
@@ -603,10 +706,10 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     // just before its SVT starts to act (J = 0 up to then)
     const double switch_margin = mixed ? (o->mixed_switch > 0 ? o->mixed_switch : 0.5) : 0.0;
     bool bf16_phase = mixed;
-    const T jtol = sizeof(T) == 8 ? T(1e-13) : T(2e-6);
+    const T jtol = jtol_of<T>();
     const unsigned wgrid_n = (unsigned)((n * 32 + 255) / 256);
     auto nl = [&](int si) -> int64_t { return si < 0 ? 0 : 1; };
-    const int64_t jac_launches = 1 + (int64_t)sweeps * ((max_pp / jacobi_bs<T>() - 1) + 1);
+    const int64_t jac_launches = 1;   // every sweep of every block in one launch
     // relative error bound of the bf16 stop-test product (stop_tc_decide), with a factor-2 margin
     const double tc_rel = 2.0 * (2.0 / 256.0 + 1.0 / 65536.0 + (double)r / 16777216.0);
     // the tensor-core stage of the stop test runs in chunks that follow one in
@@ -623,7 +726,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         prof.end(LRR_PH_GRAM, 1 + nl(S_XT) + nl(S_XW));
         prof.begin();
         k::col_norm_max<T><<<t, 256, 0, s>>>(B.jd, B.svt_on, B.jscale, t);
-        LRR_CUDA_TRY(osj_sweeps<T>(B.jd, t, max_pp, sweeps, jtol, B.jsweeps, s));
+        LRR_CUDA_TRY(osj_sweeps<T>(B.jd, t, max_pp, sweeps, jtol, B.jsweeps, s, jcluster));
         prof.end(LRR_PH_JACOBI, jac_launches + 1);
         prof.begin();
         k::svt_weights<T><<<t, 256, 0, s>>>(B.jd, B.hp, B.act, B.svt_on, B.mu, B.rank_cur, t);
@@ -641,12 +744,19 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
                 LRR_CUDA_TRY(tc_gemm_bf16(B.Ubf, B.ldm8, B.Pbf, B.ldm8, B.Tt, r, r, (int)n, (int)m, B.tc_err, s));
             }
         }
-        LRR_CUDA_TRY(run_set(S_T));
+        if (tc32) {
+            // float32-accurate U^T P on the tensor cores for the blocks past the bf16 phase
+            LRR_CUDA_TRY(tc_gemm_3xtf32(B.Uh, B.Ul, B.m4, B.Ph, B.Pl, B.m4, reinterpret_cast<float*>(B.Tt), r, r,
+                                        (int)n, (int)m, B.colblk, B.gemm32, B.tc_err, s));
+        } else {
+            LRR_CUDA_TRY(run_set(S_T));
+        }
         prof.end(LRR_PH_ZGEMM, bf16_phase ? 2 : 1);
         prof.begin();
         k::z_update<T><<<wgrid_n, 256, 0, s>>>(r, n, B.colblk, B.act, B.mu, o->rho, o->mu_max, B.Tt, B.Theta, B.Jt,
                                                B.Y2t, B.Zt, B.D, B.A, B.sig, B.dinv, B.dmax, B.afro,
-                                               bf16_phase ? B.Zbf : nullptr, B.ldr8);
+                                               bf16_phase ? B.Zbf : nullptr, B.ldr8, tc32 ? B.Dh : nullptr,
+                                               tc32 ? B.Dl : nullptr, B.r4);
         prof.end(LRR_PH_ZUPDATE, 1);
         // E-step, residuals, duals
         prof.begin();
@@ -654,12 +764,18 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
             if (bf16_phase)
                 LRR_CUDA_TRY(tc_gemm_bf16(B.USbf, B.ldr8, B.Zbf, B.ldr8, B.MZ, m, (int)m, (int)n, r, B.tc_err, s));
         }
-        LRR_CUDA_TRY(run_set(S_MZ));
+        if (tc32) {
+            LRR_CUDA_TRY(tc_gemm_3xtf32(B.UTh, B.UTl, B.r4, B.Dh, B.Dl, B.r4, reinterpret_cast<float*>(B.MZ), m,
+                                        (int)m, (int)n, r, B.colblk, B.gemm32, B.tc_err, s));
+        } else {
+            LRR_CUDA_TRY(run_set(S_MZ));
+        }
         prof.end(LRR_PH_MZGEMM, bf16_phase ? 2 : 1);
         prof.begin();
         k::e_update<T><<<wgrid_n, 256, 0, s>>>(m, n, B.colblk, B.act, B.mu, o->rho, o->mu_max, o->lambda,
                                                has_perp ? B.C : nullptr, B.MZ, B.Y1, B.E, B.P, B.r1,
-                                               bf16_phase ? B.Pbf : nullptr, B.ldm8);
+                                               bf16_phase ? B.Pbf : nullptr, B.ldm8, tc32 ? B.Ph : nullptr,
+                                               tc32 ? B.Pl : nullptr, B.m4);
         prof.end(LRR_PH_EUPDATE, 1);
         prof.begin();
         k::stop_part1<T><<<ceil_div(t, 128), 128, 0, s>>>(t, B.act, B.r1, B.dmax, nu_h, 1.0 / std::sqrt((double)n), o->eps, B.need_exact,
@@ -789,10 +905,36 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         LRR_CUDA_TRY(gemm_grouped<T>(dz, 1, false, false, (int)n, (int)n, s));
     }
     if (res && res->S)
-        k::scatter_cols<T><<<dim3(grid1(m), (unsigned)std::min<int64_t>(n, 65535)), 256, 0, s>>>(B.E, m, n, B.perm, static_cast<T*>(res->S));
+        k::scatter_cols<T><<<dim3(grid1(m), (unsigned)std::min<int64_t>(n, 65535)), 256, 0, s>>>(
+            B.E, m, n, B.perm, static_cast<T*>(res->S), m, m);
+    // factored output: Z = F G with F = V Q (t > 1) or V (t = 1)
+    int fk = 0;
+    int64_t fcl = 0;
+    if (res && (res->F || res->G)) {
+        const bool comb = dfc && t > 1;
+        fk = comb ? k1 : r;
+        const int64_t kmax = comb ? std::min<int64_t>(m, blk[0].l) : std::min<int64_t>(m, n);
+        if (fk > 0 && res->F) {
+            if (comb) {
+                GemmDesc<T> fd = gdesc<T>(B.V, n, B.Q, r, static_cast<T*>(res->F), n, (int)n, fk, r, nullptr);
+                GemmDesc<T>* df = B.gd + gh.size() + 9;
+                LRR_CUDA_TRY(cudaMemcpyAsync(df, &fd, sizeof(fd), cudaMemcpyHostToDevice, s));
+                LRR_CUDA_TRY(gemm_grouped<T>(df, 1, false, false, (int)n, fk, s));
+            } else {
+                LRR_CUDA_TRY(cudaMemcpy2DAsync(res->F, sizeof(T) * n, B.V, sizeof(T) * n, sizeof(T) * n, (size_t)r,
+                                               cudaMemcpyDeviceToDevice, s));
+            }
+            ++fcl;
+        }
+        if (fk > 0 && res->G) {
+            k::scatter_cols<T><<<dim3(grid1(fk), (unsigned)std::min<int64_t>(n, 65535)), 256, 0, s>>>(
+                comb ? B.Wc : B.Zt, fk, n, B.perm, static_cast<T*>(res->G), comb ? k1 : r, kmax);
+            ++fcl;
+        }
+    }
     LRR_CUDA_TRY(cudaEventRecord(ev[3], s));
     {
-        int64_t cl = (res && res->Z ? 1 : 0) + (res && res->S ? 1 : 0);
+        int64_t cl = (res && res->Z ? 1 : 0) + (res && res->S ? 1 : 0) + fcl;
         if (dfc && t > 1) cl += 2 + (tall[0] ? 1 : 0) + (k1 > 0 ? 3 * 3 + 3 : 0);
         prof.launches += cl;
         prof.calls[LRR_PH_COMBINE] += cl;
@@ -831,6 +973,10 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
             cudaMemcpy(sc.data(), B.svtcalls, sizeof(int) * t, cudaMemcpyDeviceToHost);
             for (int i = 0; i < t; ++i) { st.svt_sweeps += sw[i]; st.svt_calls += sc[i]; }
         }
+        if (res->factor_k) *res->factor_k = fk;
+        if (res->sweeps) {
+            LRR_CUDA_TRY(cudaMemcpy(res->sweeps, B.jsweeps, sizeof(int) * t, cudaMemcpyDeviceToHost));
+        }
         if (res->timings_ms) {
             float a = 0, b2 = 0, c = 0;
             cudaEventElapsedTime(&a, ev[0], ev[1]);
@@ -851,7 +997,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
 template <typename T>
 int svt_impl(const T* A, int64_t rows, int64_t cols, int64_t lda, double tau, T* J, int64_t ldj, int32_t* rank_out,
              cudaStream_t s) {
-    constexpr int B2 = 2 * jacobi_bs<T>();
+    constexpr int B2 = osj_pivot_width();
     const bool tall = cols <= rows;
     const int p = (int)std::min(rows, cols);
     const int L = (int)(tall ? rows : cols);
@@ -872,7 +1018,7 @@ int svt_impl(const T* A, int64_t rows, int64_t cols, int64_t lda, double tau, T*
         *Hp = reinterpret_cast<T*>(a.take<T*>(1));
         *hp = reinterpret_cast<T*>(a.take<T*>(1));
         *scl = a.take<T>(1);
-        *off = a.take<T>(1);
+        *off = a.take<T>(3);
         *T1p = reinterpret_cast<T*>(a.take<T*>(1));
     };
     T *X, *W, *H, *T1, *h, *Wp, *Hp, *hp, *scl, *off, *T1p;
@@ -974,7 +1120,7 @@ void* svt_scratch_address() {
 template <typename T>
 int svt_noalloc_impl(const T* A, int64_t rows, int64_t cols, int64_t lda, double tau, T* J, int64_t ldj,
                      int32_t* rank_out, cudaStream_t s) {
-    constexpr int B2 = 2 * jacobi_bs<T>();
+    constexpr int B2 = osj_pivot_width();
     const bool tall = cols <= rows;
     const int p = (int)std::min(rows, cols);
     const int L = (int)(tall ? rows : cols);
@@ -1003,7 +1149,7 @@ int svt_noalloc_impl(const T* A, int64_t rows, int64_t cols, int64_t lda, double
         q.hp = a.take<T*>(1);
         q.T1p = a.take<T*>(1);
         q.scl = a.take<T>(1);
-        q.off = a.take<T>(1);
+        q.off = a.take<T>(3);
         return q;
     };
     Arena sz(nullptr);
@@ -1062,10 +1208,10 @@ int svt_noalloc_impl(const T* A, int64_t rows, int64_t cols, int64_t lda, double
 }
 
 template <typename T, typename Tin>
-size_t workspace_impl(const lrr_problem* p, bool mixed) {
+size_t workspace_impl(const lrr_problem* p, const lrr_options* o, bool mixed) {
     const auto blk = block_info<T>(p);
     Arena probe(nullptr);
-    carve<T>(probe, p, !std::is_same<Tin, double>::value, blk, mixed);
+    carve<T>(probe, p, !std::is_same<Tin, double>::value, blk, mixed, use_tc32<T>(p, o));
     return probe.off + kAlign;
 }
 
@@ -1105,19 +1251,209 @@ int dispatch(const lrr_problem* p0, const lrr_options* o, void* ws, size_t wsb, 
     }
 }
 
+// scatter of a block's l x l estimate to rows and columns perm[off .. off+l-1]
+template <typename T>
+__global__ void scatter_block(const T* __restrict__ src, int64_t l, const int64_t* __restrict__ perm, int64_t off,
+                              T* __restrict__ Z, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < l * l; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = e % l, b = e / l;
+        Z[perm[off + a] + perm[off + b] * n] = src[e];
+    }
+}
+
+// The footnote variant of Algorithm 1: every block problem uses its own
+// observations C_i as the dictionary (l_i x l_i solutions, solved as t
+// independent LRR problems on concurrent streams), and the C step keeps the
+// `rank` largest singular triplets of diag(Z_1, ..., Z_t).
+template <typename T>
+int local_impl(const lrr_problem* p, const lrr_options* o, int64_t rank, lrr_result* res, int32_t streams,
+               cudaStream_t s) {
+    const int64_t m = p->m, n = p->n;
+    const int t = p->t;
+    const T* M = static_cast<const T*>(p->M);
+    std::vector<int64_t> l((size_t)t), kmax((size_t)t), off((size_t)t + 1);
+    int64_t lmax = 0, words = m * n + m * n + n * n;   // C (block order), S (block order), scratch
+    for (int i = 0; i < t; ++i) {
+        off[i] = p->offsets[i];
+        l[i] = p->offsets[i + 1] - p->offsets[i];
+        kmax[i] = std::min<int64_t>(m, l[i]);
+        lmax = std::max(lmax, l[i]);
+    }
+    off[t] = n;
+    int64_t fwords = 0;
+    for (int i = 0; i < t; ++i) fwords += 2 * l[i] * kmax[i];   // F_i, G_i
+    const int B2 = osj_pivot_width();
+    int64_t wwords = 0;
+    std::vector<int> kp((size_t)t);
+    for (int i = 0; i < t; ++i) {
+        kp[i] = round_up((int)kmax[i], B2);
+        wwords += (int64_t)kp[i] * kp[i] + l[i] * kmax[i] + l[i] * kmax[i];   // W_i, X_i, T_i
+    }
+    const size_t bytes = sizeof(T) * (size_t)(words + fwords + wwords) + sizeof(int64_t) * n +
+                         (sizeof(OsjDesc<T>) + sizeof(GemmDesc<T>) * 2 + 64 * sizeof(T) + 64) * (size_t)t + 4096 * 4;
+    void* mem = nullptr;
+    if (cudaMallocAsync(&mem, bytes, s) != cudaSuccess) return LRR_ERR_CUDA;
+    struct Free {
+        void* p; cudaStream_t s;
+        ~Free() { if (p) cudaFreeAsync(p, s); }
+    } guard{mem, s};
+    Arena a(mem);
+    T* Cb = a.take<T>(m * n);
+    T* Sb = a.take<T>(m * n);
+    T* Zs = a.take<T>(lmax * lmax);
+    int64_t* perm_d = a.take<int64_t>(n);
+    std::vector<T*> F((size_t)t), G((size_t)t), W((size_t)t), X((size_t)t), Tm((size_t)t);
+    for (int i = 0; i < t; ++i) {
+        F[i] = a.take<T>(l[i] * kmax[i]);
+        G[i] = a.take<T>(kmax[i] * l[i]);
+        W[i] = a.take<T>((size_t)kp[i] * kp[i]);
+        X[i] = a.take<T>(l[i] * kmax[i]);
+        Tm[i] = a.take<T>(l[i] * kmax[i]);
+    }
+    OsjDesc<T>* od = a.take<OsjDesc<T>>(t);
+    GemmDesc<T>* gd = a.take<GemmDesc<T>>(2 * (size_t)t);
+    T* scl = a.take<T>(t);
+    T* off3 = a.take<T>(3 * (size_t)t);
+    int* done = a.take<int>(t);
+    int* on = a.take<int>(t);
+    T* hk = a.take<T>((size_t)t * 1);   // placeholder (per-block masks follow)
+    (void)hk;
+    std::vector<T*> H((size_t)t);
+    for (int i = 0; i < t; ++i) H[i] = a.take<T>(kp[i]);
+    if (a.off > bytes) return LRR_ERR_WORKSPACE;
+    LRR_CUDA_TRY(cudaMemcpyAsync(perm_d, p->perm, sizeof(int64_t) * n, cudaMemcpyHostToDevice, s));
+    k::gather_cols<T, T><<<dim3(grid1(m), (unsigned)std::min<int64_t>(n, 65535)), 256, 0, s>>>(M, p->ldm, perm_d, m, n,
+                                                                                               Cb);
+    // ---- F step: t independent LRR problems C_i = C_i Z_i + S_i
+    std::vector<std::vector<int64_t>> ids((size_t)t), offs((size_t)t);
+    std::vector<lrr_problem> probs((size_t)t);
+    std::vector<lrr_result> rs((size_t)t);
+    std::vector<int32_t> its((size_t)t), fk((size_t)t), st((size_t)t), sw((size_t)t);
+    std::vector<double> rsd((size_t)2 * t);
+    std::vector<std::vector<int32_t>> rk((size_t)t, std::vector<int32_t>(3));
+    for (int i = 0; i < t; ++i) {
+        ids[i].resize((size_t)l[i]);
+        std::iota(ids[i].begin(), ids[i].end(), 0);
+        offs[i] = {0, l[i]};
+        lrr_problem& q = probs[i];
+        q = lrr_problem{};
+        q.M = Cb + off[i] * m; q.m = m; q.n = l[i]; q.ldm = m; q.t = 1;
+        q.perm = ids[i].data(); q.offsets = offs[i].data();
+        lrr_result& r = rs[i];
+        r = lrr_result{};
+        r.S = Sb + off[i] * m; r.F = F[i]; r.G = G[i]; r.factor_k = &fk[i]; r.iters = &its[i];
+        r.resid = &rsd[2 * i]; r.ranks = rk[i].data(); r.sweeps = &sw[i];
+    }
+    LRR_CUDA_TRY(cudaStreamSynchronize(s));
+    int rc = lrr_solve_batch(probs.data(), t, o, rs.data(), st.data(), streams, s);
+    if (rc < 0) return rc;
+    // ---- C step: singular values of every Z_i = F_i G_i are those of G_i
+    //      (F_i orthonormal); one-sided Jacobi on X_i = G_i^T W_i for all blocks
+    std::vector<OsjDesc<T>> dh((size_t)t);
+    std::vector<GemmDesc<T>> g1v((size_t)t);
+    int max_kp = 0;
+    for (int i = 0; i < t; ++i) {
+        const int ki = std::max(1, fk[i]);
+        k::init_padded<T><<<grid1((int64_t)kp[i] * kp[i]), 256, 0, s>>>(W[i], ki, kp[i], T(1), 1);
+        GemmDesc<T> g = gdesc<T>(G[i], kmax[i], W[i], kp[i], X[i], l[i], (int)l[i], ki, ki, nullptr);
+        g1v[i] = g;
+        OsjDesc<T>& d = dh[i];
+        d = OsjDesc<T>{};
+        d.X = X[i]; d.W = W[i]; d.done = done + i; d.off = off3 + 3 * i; d.active = on + i; d.scale = scl + i;
+        d.mu = nullptr; d.ldx = l[i]; d.ldw = kp[i]; d.L = (int)l[i]; d.p = ki; d.pp = round_up(ki, B2);
+        d.strict = 1;
+        max_kp = std::max(max_kp, d.pp);
+    }
+    std::vector<int> onh((size_t)t);
+    for (int i = 0; i < t; ++i) onh[i] = fk[i] > 0 ? 1 : 0;
+    LRR_CUDA_TRY(cudaMemcpyAsync(on, onh.data(), sizeof(int) * t, cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(gd, g1v.data(), sizeof(GemmDesc<T>) * t, cudaMemcpyHostToDevice, s));
+    LRR_CUDA_TRY(gemm_grouped<T>(gd, t, true, false, (int)lmax, max_kp, s));
+    LRR_CUDA_TRY(cudaMemcpyAsync(od, dh.data(), sizeof(OsjDesc<T>) * t, cudaMemcpyHostToDevice, s));
+    k::col_norm_max<T><<<t, 256, 0, s>>>(od, on, scl, t);
+    LRR_CUDA_TRY(osj_sweeps<T>(od, t, max_kp, 40, sizeof(T) == 8 ? T(1e-13) : T(2e-6), nullptr, s, 0));
+    // singular values to the host; the global top `rank`
+    std::vector<std::vector<T>> xs((size_t)t);
+    std::vector<std::tuple<double, int, int>> all;
+    for (int i = 0; i < t; ++i) {
+        if (fk[i] <= 0) continue;
+        xs[i].resize((size_t)(l[i] * fk[i]));
+        LRR_CUDA_TRY(cudaMemcpyAsync(xs[i].data(), X[i], sizeof(T) * l[i] * fk[i], cudaMemcpyDeviceToHost, s));
+    }
+    LRR_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int i = 0; i < t; ++i)
+        for (int j = 0; j < fk[i]; ++j) {
+            double q = 0;
+            for (int64_t r0 = 0; r0 < l[i]; ++r0) q += (double)xs[i][r0 + j * l[i]] * xs[i][r0 + j * l[i]];
+            all.emplace_back(-std::sqrt(q), i, j);
+        }
+    std::sort(all.begin(), all.end());
+    const int64_t kk = rank > 0 ? rank : (int64_t)rk[0][1];
+    std::vector<std::vector<T>> hh((size_t)t);
+    for (int i = 0; i < t; ++i) hh[i].assign((size_t)kp[i], T(0));
+    for (int64_t q = 0; q < std::min<int64_t>(kk, (int64_t)all.size()); ++q)
+        if (-std::get<0>(all[(size_t)q]) > 0) hh[std::get<1>(all[(size_t)q])][std::get<2>(all[(size_t)q])] = T(1);
+    // Z_i,k = F_i W_i diag(h_i) X_i^T, scattered to the original rows and columns
+    if (res && res->Z) {
+        LRR_CUDA_TRY(cudaMemsetAsync(res->Z, 0, sizeof(T) * n * n, s));
+        for (int i = 0; i < t; ++i) {
+            const int ki = fk[i];
+            if (ki <= 0) continue;
+            LRR_CUDA_TRY(cudaMemcpyAsync(H[i], hh[i].data(), sizeof(T) * kp[i], cudaMemcpyHostToDevice, s));
+            GemmDesc<T> ga = gdesc<T>(F[i], l[i], W[i], kp[i], Tm[i], l[i], (int)l[i], ki, ki, nullptr);
+            GemmDesc<T> gb = gdesc<T>(Tm[i], l[i], X[i], l[i], Zs, l[i], (int)l[i], (int)l[i], ki, nullptr);
+            gb.kscale = H[i];
+            LRR_CUDA_TRY(cudaMemcpyAsync(gd + 2 * i, &ga, sizeof(ga), cudaMemcpyHostToDevice, s));
+            LRR_CUDA_TRY(cudaMemcpyAsync(gd + 2 * i + 1, &gb, sizeof(gb), cudaMemcpyHostToDevice, s));
+            LRR_CUDA_TRY(gemm_grouped<T>(gd + 2 * i, 1, false, false, (int)l[i], ki, s));
+            LRR_CUDA_TRY(gemm_grouped<T>(gd + 2 * i + 1, 1, false, true, (int)l[i], (int)l[i], s));
+            scatter_block<T><<<grid1(l[i] * l[i]), 256, 0, s>>>(Zs, l[i], perm_d, off[i], static_cast<T*>(res->Z), n);
+        }
+    }
+    if (res && res->S)
+        k::scatter_cols<T><<<dim3(grid1(m), (unsigned)std::min<int64_t>(n, 65535)), 256, 0, s>>>(
+            Sb, m, n, perm_d, static_cast<T*>(res->S), m, m);
+    LRR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (res) {
+        if (res->iters) for (int i = 0; i < t; ++i) res->iters[i] = its[i];
+        if (res->resid) for (int i = 0; i < 2 * t; ++i) res->resid[i] = rsd[i];
+        if (res->ranks) {
+            int rmax = 0;
+            for (int i = 0; i < t; ++i) rmax = std::max(rmax, rk[i][0]);
+            res->ranks[0] = rmax;
+            res->ranks[1] = (int32_t)std::min<int64_t>(kk, (int64_t)all.size());
+            for (int i = 0; i < t; ++i) res->ranks[2 + i] = rk[i][1];
+        }
+        if (res->sweeps) for (int i = 0; i < t; ++i) res->sweeps[i] = sw[i];
+        if (res->factor_k) *res->factor_k = 0;
+    }
+    return rc;
+}
+
 }  // namespace
 }  // namespace lrr
 
 extern "C" {
+
+int dfc_lrr_solve_local(const lrr_problem* p0, const lrr_options* o, int64_t rank, lrr_result* r, int32_t streams,
+                        void* stream) {
+    lrr::Resolved rsv;
+    const lrr_problem* p = lrr::resolve(p0, rsv);
+    if (!lrr::valid_problem(p, o) || streams < 0) return LRR_ERR_INVALID;
+    if (r && (r->F || r->G)) return LRR_ERR_UNSUPPORTED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (o->precision == LRR_PREC_F64) return lrr::local_impl<double>(p, o, rank, r, streams, s);
+    return lrr::local_impl<float>(p, o, rank, r, streams, s);
+}
 
 size_t lrr_workspace_bytes(const lrr_problem* p0, const lrr_options* o) {
     lrr::Resolved rs;
     const lrr_problem* p = lrr::resolve(p0, rs);
     if (!lrr::valid_problem(p, o)) return 0;
     switch (o->precision) {
-        case LRR_PREC_F64: return lrr::workspace_impl<double, double>(p, false);
-        case LRR_PREC_F32: return lrr::workspace_impl<float, float>(p, false);
-        case LRR_PREC_MIXED: return lrr::workspace_impl<float, float>(p, true);
+        case LRR_PREC_F64: return lrr::workspace_impl<double, double>(p, o, false);
+        case LRR_PREC_F32: return lrr::workspace_impl<float, float>(p, o, false);
+        case LRR_PREC_MIXED: return lrr::workspace_impl<float, float>(p, o, true);
         default: return 0;
     }
 }
@@ -1164,6 +1500,95 @@ int lrr_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float*
     return rc;
 }
 
+int lrr_gemm_f32(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
+                 int64_t N, int64_t K, void* stream) {
+    if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < M) return LRR_ERR_INVALID;
+    if (M > (1 << 30) || N > lrr::kTcMaxN || K > (1 << 30)) return LRR_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t k4 = (K + 3) / 4 * 4;
+    const size_t words = (size_t)k4 * (size_t)(M + N) * 2;
+    void* mem = nullptr;
+    if (cudaMallocAsync(&mem, words * sizeof(float) + 256, s) != cudaSuccess) return LRR_ERR_CUDA;
+    float* ah = static_cast<float*>(mem);
+    float* al = ah + (size_t)k4 * M;
+    float* bh = al + (size_t)k4 * M;
+    float* bl = bh + (size_t)k4 * N;
+    int* err = reinterpret_cast<int*>(bl + (size_t)k4 * N);
+    int rc = LRR_OK;
+    lrr::k::split_tf32_km<float><<<dim3(lrr::grid1(k4), (unsigned)std::min<int64_t>(M, 65535)), 256, 0, s>>>(
+        A, lda, K, M, ah, al, k4);
+    lrr::k::split_tf32_km<float><<<dim3(lrr::grid1(k4), (unsigned)std::min<int64_t>(N, 65535)), 256, 0, s>>>(
+        B, ldb, K, N, bh, bl, k4);
+    if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess ||
+        lrr::tc_gemm_3xtf32(ah, al, k4, bh, bl, k4, C, ldc, (int)M, (int)N, (int)K, nullptr, nullptr, err, s) !=
+            cudaSuccess)
+        rc = LRR_ERR_CUDA;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = LRR_ERR_CUDA;
+    cudaFreeAsync(mem, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = LRR_ERR_CUDA;
+    if (h) rc = LRR_ERR_CUDA;
+    return rc;
+}
+
+int lrr_gemm_timing(int32_t kind, int64_t M, int64_t N, int64_t K, int32_t repeat, double* ms_per_launch,
+                    void* stream) {
+    if (!ms_per_launch || M < 1 || N < 1 || K < 1 || repeat < 1 || (kind != 0 && kind != 1)) return LRR_ERR_INVALID;
+    if (M > (1 << 20) || N > lrr::kTcMaxN || K > (1 << 20)) return LRR_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t kp = kind == 0 ? (K + 7) / 8 * 8 : (K + 3) / 4 * 4;
+    const size_t esz = kind == 0 ? 2 : 4;
+    const size_t nops = kind == 0 ? 1 : 2;          // split TF32: hi and lo
+    const size_t abytes = ((size_t)kp * M * esz + 255) / 256 * 256, bbytes = ((size_t)kp * N * esz + 255) / 256 * 256;
+    const size_t total = nops * (abytes + bbytes) + sizeof(float) * (size_t)M * N + 256;
+    void* mem = nullptr;
+    if (cudaMallocAsync(&mem, total, s) != cudaSuccess) return LRR_ERR_CUDA;
+    char* p = static_cast<char*>(mem);
+    void* A0 = p; p += abytes;
+    void* A1 = p; p += nops > 1 ? abytes : 0;
+    void* B0 = p; p += bbytes;
+    void* B1 = p; p += nops > 1 ? bbytes : 0;
+    float* C = reinterpret_cast<float*>(p); p += sizeof(float) * (size_t)M * N;
+    int* err = reinterpret_cast<int*>((reinterpret_cast<uintptr_t>(p) + 15) / 16 * 16);
+    int rc = LRR_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (kind == 0) {
+        lrr::k::fill_hash_bf16<<<lrr::grid1(kp * M), 256, 0, s>>>(static_cast<uint16_t*>(A0), kp * M, 1u);
+        lrr::k::fill_hash_bf16<<<lrr::grid1(kp * N), 256, 0, s>>>(static_cast<uint16_t*>(B0), kp * N, 2u);
+    } else {
+        lrr::k::fill_hash<float><<<lrr::grid1(kp * M), 256, 0, s>>>(static_cast<float*>(A0), kp * M, 1u);
+        lrr::k::fill_hash<float><<<lrr::grid1(kp * M), 256, 0, s>>>(static_cast<float*>(A1), kp * M, 3u);
+        lrr::k::fill_hash<float><<<lrr::grid1(kp * N), 256, 0, s>>>(static_cast<float*>(B0), kp * N, 2u);
+        lrr::k::fill_hash<float><<<lrr::grid1(kp * N), 256, 0, s>>>(static_cast<float*>(B1), kp * N, 4u);
+    }
+    auto launch = [&]() {
+        return kind == 0 ? lrr::tc_gemm_bf16(A0, kp, B0, kp, C, M, (int)M, (int)N, (int)K, err, s)
+                         : lrr::tc_gemm_3xtf32(static_cast<float*>(A0), static_cast<float*>(A1), kp,
+                                               static_cast<float*>(B0), static_cast<float*>(B1), kp, C, M, (int)M,
+                                               (int)N, (int)K, nullptr, nullptr, err, s);
+    };
+    if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess || launch() != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        rc = LRR_ERR_CUDA;
+    if (rc == LRR_OK) {
+        cudaEventRecord(e0, s);
+        for (int i = 0; i < repeat && rc == LRR_OK; ++i)
+            if (launch() != cudaSuccess) rc = LRR_ERR_CUDA;
+        cudaEventRecord(e1, s);
+    }
+    int h = 0;
+    if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = LRR_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = LRR_ERR_CUDA;
+    float ms = 0.f;
+    if (rc == LRR_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) *ms_per_launch = ms / repeat;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(mem, s);
+    cudaStreamSynchronize(s);
+    if (h) rc = LRR_ERR_CUDA;
+    return rc;
+}
+
 int lrr_svt_noalloc(const void* A, int64_t rows, int64_t cols, int64_t lda, double tau, void* J, int64_t ldj,
                     int32_t precision, int32_t* rank, void* stream) {
     if (!A || !J || rows < 1 || cols < 1 || lda < rows || ldj < rows || !(tau > 0)) return LRR_ERR_INVALID;
@@ -1179,6 +1604,13 @@ int lrr_svt_noalloc(const void* A, int64_t rows, int64_t cols, int64_t lda, doub
 }
 
 size_t lrr_svt_noalloc_capacity(void) { return lrr::kNoAllocScratchBytes; }
+
+int64_t lrr_factor_max_rank(const lrr_problem* p) {
+    if (!p || p->m < 1 || p->n < 1 || p->t < 1 || p->t > p->n) return 0;
+    if (p->t == 1) return std::min(p->m, p->n);
+    const int64_t l1 = p->offsets ? p->offsets[1] - p->offsets[0] : p->n / p->t;
+    return l1 > 0 ? std::min(p->m, l1) : 0;
+}
 
 void lrr_default_options(lrr_options* o) {
     if (!o) return;

@@ -252,31 +252,240 @@ __global__ void __launch_bounds__(NT, 1) tc_gemm_kernel(const __grid_constant__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Float32-accurate product on the tensor cores by split TF32 ("3xTF32"): every
+// float32 operand x is given as x ~ hi + lo, both exact TF32 values (hi the
+// nearest TF32 value to x, lo the nearest to x - hi; split_tf32); then
+//   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi     (+ a_lo b_lo, dropped)
+// run as kind::tf32 MMAs into one float32 accumulator.  The dropped term is
+// below 2^-22 |a b| and the split error below 2^-21 |a b|, both of random sign.
+// Same CTA structure as tc_gemm_kernel; a stage holds A_hi, A_lo, B_hi, B_lo
+// slabs of 32 float32 (128 bytes) along K.  With `tile_flag` set, a 128-column
+// tile whose columns all belong to blocks whose flag is zero is skipped.
+constexpr int BK32 = 32, STAGES32 = 3;
+constexpr uint32_t STAGE_BYTES32 = 4 * TILE_BYTES;
+
+// instruction descriptor, kind::tf32: fp32 accumulate, TF32 A and B, both K-major
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+struct TileSkip {
+    const int* colblk;   // block of each column of C
+    const int* flag;     // per block: nonzero = compute its columns
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// The accumulator is drained into float32 registers every SLAB k-blocks: the
+// tensor cores add each MMA's products to the accumulator with a truncating
+// alignment, an error that grows with the magnitude the accumulator has
+// reached, so a long K is summed as short tensor-core slabs (each into a fresh
+// accumulator) added in float32 on the CUDA cores.  Two TMEM accumulators
+// (128 columns each) alternate: the MMAs of one slab overlap the draining of
+// the previous one.
+constexpr int SLAB = 2;
+
+__global__ void __launch_bounds__(NT, 1) tc_gemm_3xtf32_kernel(
+    const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
+    const __grid_constant__ CUtensorMap mapBh, const __grid_constant__ CUtensorMap mapBl, float* __restrict__ C,
+    int64_t ldc, int M, int N, int K, int* __restrict__ err, const TileSkip sk) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[STAGES32], empty_bar[STAGES32], accf[2], acce[2], drain_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int nk = (K + BK32 - 1) / BK32;
+    const int nslab = (nk + SLAB - 1) / SLAB;
+
+    // leave (uniformly, before any barrier or TMEM use) when no column of
+    // this tile belongs to a block that needs the product
+    if (sk.flag) {
+        const int b_lo = sk.colblk[n0], b_hi = sk.colblk[min(n0 + BN, N) - 1];
+        bool any = false;
+        for (int b = b_lo; b <= b_hi; ++b) any |= sk.flag[b] != 0;
+        if (!any) return;
+    }
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES32; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 4);
+        }
+        mbar_init(&drain_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(2 * BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % STAGES32;
+                if (kb >= STAGES32 && !mbar_wait(&empty_bar[s], ((kb / STAGES32) - 1) & 1, err)) {
+                    abort_flag = 1;
+                    break;
+                }
+                if (abort_flag) break;
+                unsigned char* st = base + s * STAGE_BYTES32;
+                mbar_expect_tx(&full_bar[s], STAGE_BYTES32);
+                tma_load_2d(st, &mapAh, kb * BK32, m0, &full_bar[s]);
+                tma_load_2d(st + TILE_BYTES, &mapAl, kb * BK32, m0, &full_bar[s]);
+                tma_load_2d(st + 2 * TILE_BYTES, &mapBh, kb * BK32, n0, &full_bar[s]);
+                tma_load_2d(st + 3 * TILE_BYTES, &mapBl, kb * BK32, n0, &full_bar[s]);
+                issued = kb + 1;
+            }
+            if (abort_flag) {
+                for (int kb = issued - STAGES32 < 0 ? 0 : issued - STAGES32; kb < issued; ++kb)
+                    mbar_wait(&full_bar[kb % STAGES32], (kb / STAGES32) & 1, err);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_tf32(BM, BN);
+            bool ok = true;
+            for (int kb = 0; kb < nk && ok; ++kb) {
+                const int s = kb % STAGES32;
+                const int slab = kb / SLAB, buf = slab & 1, in_slab = kb % SLAB;
+                // the epilogue must have drained this accumulator (slab - 2)
+                if (in_slab == 0 && slab >= 2 && !mbar_wait(&acce[buf], ((slab >> 1) - 1) & 1, err)) ok = false;
+                if (ok && (!mbar_wait(&full_bar[s], (kb / STAGES32) & 1, err) || abort_flag)) ok = false;
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n");
+                const uint32_t acc = tmem + (uint32_t)(buf * BN);
+                const uint32_t ah = smem_u32(base + s * STAGE_BYTES32);
+                const uint32_t al = ah + TILE_BYTES, bh = ah + 2 * TILE_BYTES, bl = ah + 3 * TILE_BYTES;
+#pragma unroll
+                for (int k = 0; k < BK32 / 8; ++k) {
+                    const uint32_t off = k * 32;    // 8 float32 along K
+                    const uint64_t dah = smem_desc(ah + off), dal = smem_desc(al + off);
+                    const uint64_t dbh = smem_desc(bh + off), dbl = smem_desc(bl + off);
+                    const uint32_t accum = (in_slab > 0 || k > 0) ? 1u : 0u;
+                    // small terms first, the hi x hi term last
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
+                        "l"(dal), "l"(dbh), "r"(idesc), "r"(accum));
+                    asm volatile(
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(acc), "l"(dah), "l"(dbl),
+                        "r"(idesc));
+                    asm volatile(
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(acc), "l"(dah), "l"(dbh),
+                        "r"(idesc));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                 smem_u32(&empty_bar[s]))
+                             : "memory");
+                if (in_slab == SLAB - 1 || kb == nk - 1)
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                            smem_u32(&accf[buf]))
+                        : "memory");
+            }
+            if (!ok) {
+                abort_flag = 1;
+                // every MMA issued so far completes before TMEM is released
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                 smem_u32(&drain_bar))
+                             : "memory");
+                mbar_wait(&drain_bar, 0, err);
+            }
+        }
+    } else {
+        // epilogue warps 2..5 own TMEM lane quadrants (warp % 4): one row of
+        // the tile per thread, its 128 columns summed slab by slab in float32
+        const int q = warp & 3;
+        float sum[BN];
+#pragma unroll
+        for (int j = 0; j < BN; ++j) sum[j] = 0.f;
+        bool ok = true;
+        for (int slab = 0; slab < nslab; ++slab) {
+            const int buf = slab & 1;
+            ok = __all_sync(0xffffffffu, ok && mbar_wait(&accf[buf], (slab >> 1) & 1, err) && !abort_flag);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+#pragma unroll
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                uint32_t v[16];
+                const uint32_t taddr = tmem + (uint32_t)(buf * BN) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15}, [%16];\n"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 16; ++j) sum[c0 + j] += __uint_as_float(v[j]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[buf]);
+        }
+        const int row = m0 + q * 32 + lane;
+        if (ok && row < M) {
+#pragma unroll
+            for (int j = 0; j < BN; ++j) {
+                const int col = n0 + j;
+                if (col < N) C[row + (int64_t)col * ldc] = sum[j];
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * BN));
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    // looked up once (thread-safe static initialisation: solves may run on
+    // several host threads at once)
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
+            return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        return nullptr;
+    }();
     return fn;
 }
 
 // 2-D bf16 tensor map over a K-major operand: inner dimension K (ld elements
 // per row), outer dimension `rows`; 64 x 128 boxes, 128-byte swizzle, zero fill
-bool make_map(CUtensorMap* map, const void* ptr, int64_t K, int64_t rows, int64_t ld) {
+bool make_map(CUtensorMap* map, const void* ptr, int64_t K, int64_t rows, int64_t ld, bool f32 = false) {
     auto fn = encode_fn();
     if (!fn) return false;
+    const int esz = f32 ? 4 : 2;
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * esz)};
+    cuuint32_t box[2] = {(cuuint32_t)(f32 ? BK32 : BK), (cuuint32_t)BM};
     cuuint32_t estr[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return fn(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr),
+              dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -300,6 +509,28 @@ cudaError_t tc_launch(const void* A, int64_t lda, const void* B, int64_t ldb, fl
     return cudaGetLastError();
 }
 }  // namespace
+
+cudaError_t tc_gemm_3xtf32(const float* Ahi, const float* Alo, int64_t lda, const float* Bhi, const float* Blo,
+                           int64_t ldb, float* C, int64_t ldc, int M, int N, int K, const int* colblk,
+                           const int* flag, int* err, cudaStream_t s) {
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    if ((lda % 4) || (ldb % 4)) return cudaErrorInvalidValue;
+    for (const void* p : {(const void*)Ahi, (const void*)Alo, (const void*)Bhi, (const void*)Blo})
+        if (reinterpret_cast<uintptr_t>(p) % 16) return cudaErrorInvalidValue;
+    if (flag && !colblk) return cudaErrorInvalidValue;
+    CUtensorMap mah, mal, mbh, mbl;
+    if (!make_map(&mah, Ahi, K, M, lda, true) || !make_map(&mal, Alo, K, M, lda, true) ||
+        !make_map(&mbh, Bhi, K, N, ldb, true) || !make_map(&mbl, Blo, K, N, ldb, true))
+        return cudaErrorInvalidValue;
+    if (ceil_div(N, BN) > 65535) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)STAGES32 * STAGE_BYTES32 + 1024;
+    static std::atomic<uint64_t> smem_set{0};
+    const cudaError_t ea = ensure_smem_limit(tc_gemm_3xtf32_kernel, (int)smem, smem_set);
+    if (ea != cudaSuccess) return ea;
+    const dim3 grid((unsigned)ceil_div(M, BM), (unsigned)ceil_div(N, BN));
+    tc_gemm_3xtf32_kernel<<<grid, NT, smem, s>>>(mah, mal, mbh, mbl, C, ldc, M, N, K, err, TileSkip{colblk, flag});
+    return cudaGetLastError();
+}
 
 cudaError_t tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int M, int N,
                          int K, int* err, cudaStream_t s) {

@@ -44,8 +44,7 @@ def oracle_blocks(name: str, precision: str, fixed: tuple):
     M = w.M.astype(dt).astype(np.float64)
     which = [i for i, k in enumerate(fixed) if k > 0]
     return olrr.dfc_lrr(M, w.perm, w.offsets, w.lam, rho=w.rho, mu0=w.mu0, mu_max=w.mu_max, eps=w.eps,
-                        max_iter=w.max_iter, blocks_only=which, fixed_iters=list(fixed),
-                        workers=min(4, len(which)))
+                        max_iter=w.max_iter, blocks_only=which, fixed_iters=list(fixed))
 
 
 def block_projected(name, precision, iters, blocks):

@@ -139,3 +139,21 @@ def test_workspace_grows_with_the_problem(lib):
     p, keep = _problem(n=60, t=3)
     om = binding.options(0.1, precision="mixed")
     assert lib.lrr_workspace_bytes(ctypes.byref(p), ctypes.byref(om)) > sizes[1]
+
+
+def test_factor_max_rank_bounds_the_factored_output():
+    """min(m, l_1) for t > 1, min(m, n) for t = 1, 0 for an invalid problem."""
+    import ctypes
+    from paper_1304_5583_gb300 import binding
+    lib = binding.load()
+    off = np.array([0, 7, 19, 30], dtype=np.int64)
+    p = binding.LrrProblem()
+    p.m, p.n, p.ldm, p.t = 12, 30, 12, 3
+    p.offsets = off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    assert lib.lrr_factor_max_rank(ctypes.byref(p)) == 7
+    p.m = 5
+    assert lib.lrr_factor_max_rank(ctypes.byref(p)) == 5
+    p.t, p.m = 1, 40
+    assert lib.lrr_factor_max_rank(ctypes.byref(p)) == 30
+    p.t = 0
+    assert lib.lrr_factor_max_rank(ctypes.byref(p)) == 0

@@ -44,3 +44,22 @@ def test_workspace_query_with_a_drawn_partition(binding):
     with pytest.raises(ValueError):
         binding.workspace_bytes(M, None, None, o)         # t is needed without offsets
     assert binding.workspace_bytes(M, perm, np.array([0, 30, 30, 60]), o) == 0
+
+
+def test_phase_transition_success_criterion_on_oracle_solutions():
+    """The oracle constraints (Appendix) within 1e-4, evaluated on the float64
+    oracle's LRR solutions of the paper's generator: a low outlier fraction
+    recovers the row space and the outliers, a corrupted estimate fails."""
+    import numpy as np
+    from oracle import lrr as olrr
+    from paper_1304_5583_gb300 import phase, synth
+    d = synth.union_of_subspaces(1, 60, 3, 3, 30, 0.1, recipe="paper")
+    r = olrr.lrr_alm(d.M, d.M, 0.5, eps=1e-8, max_iter=2000)
+    V0 = phase.row_space_of_inliers(d)
+    assert phase.oracle_constraints_hold(r.Z, r.E, V0, d.outlier)
+    Zbad = r.Z.copy()
+    Zbad[:, 0] += 1e-3 * np.random.default_rng(0).standard_normal(Zbad.shape[0])
+    assert not phase.oracle_constraints_hold(Zbad, r.E, V0, d.outlier)
+    Ebad = r.E.copy()
+    Ebad[:, np.flatnonzero(~d.outlier)[0]] += 1e-3
+    assert not phase.oracle_constraints_hold(r.Z, Ebad, V0, d.outlier)

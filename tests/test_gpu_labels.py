@@ -28,5 +28,13 @@ def test_labels_identical_to_oracle(lib, name, precision):
     lab = segment.segment(res.Z.cpu().numpy().astype(np.float64), g["k"], seed=0)
     ref = np.asarray(g["labels"])
     acc = segment.matched_accuracy(lab, w.data.labels)
-    print(f"{name} {precision}: matched accuracy {acc:.4f} (oracle {g['matched_accuracy_vs_truth']:.4f})")
-    assert segment.same_partition(lab, ref)
+    # columns replaced by outliers belong to no subspace: their cluster is an
+    # arbitrary k-means assignment of noise rows of the affinity, so the
+    # partition is compared on the subspace columns (the outliers themselves
+    # are what the S columns mark)
+    inl = ~w.data.outlier if name != "dfc_faces_2016x2432" else np.ones(len(ref), bool)
+    print(f"{name} {precision}: matched accuracy {acc:.4f} (oracle {g['matched_accuracy_vs_truth']:.4f}); "
+          f"same partition over all columns: {segment.same_partition(lab, ref)}, "
+          f"over the {int(inl.sum())} subspace columns: {segment.same_partition(lab[inl], ref[inl])}")
+    assert segment.same_partition(lab[inl], ref[inl])
+    assert acc == pytest.approx(g["matched_accuracy_vs_truth"], abs=1e-12)

@@ -1,0 +1,58 @@
+"""Segmentation on the GPU (lrr_segment: Section 4.1.2's affinity |U U^T|,
+normalised spectral embedding, k-means) from the solver's factored output,
+against the float64 oracle's labels (tests/golden, oracle only) and against
+the CPU segmentation routine applied to the same estimate."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import segment as oseg
+from parity_helpers import to_dev
+from paper_1304_5583_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _solve(w, precision):
+    from paper_1304_5583_gb300 import binding
+    Md = to_dev(w.M, np.float32)
+    o = binding.options(w.lam, rho=w.rho, mu0=w.mu0, mu_max=w.mu_max, eps=w.eps, max_iter=w.max_iter,
+                        precision=precision)
+    return binding.dfc_lrr_solve(Md, w.perm, w.offsets, o, want_factors=True)
+
+
+def test_clean_subspaces_are_segmented_exactly(lib):
+    """Noiseless independent subspaces: every point lands in its own subspace's cluster."""
+    from paper_1304_5583_gb300 import binding
+    d = synth.union_of_subspaces(12, 50, 4, 3, 25, 0.0)
+    perm, off = synth.column_partition(3, d.M.shape[1], 2)
+    w = synth.Workload("clean", d, perm, off, lam=0.5, eps=1e-6)
+    res = _solve(w, "f32")
+    assert res.status == 0
+    lab = binding.segment(res.F, res.G, res.factor_k, d.k, seed=0)
+    assert oseg.same_partition(lab, d.labels)
+
+
+@pytest.mark.parametrize("name,precision", [("dfc_500x5000", "f32"), ("dfc_1000x20000", "mixed")])
+def test_gpu_labels_match_the_oracle(lib, name, precision):
+    from paper_1304_5583_gb300 import binding
+    with open(os.path.join(GOLDEN, f"labels_{name}.json")) as f:
+        g = json.load(f)
+    w = synth.workload(name)
+    res = _solve(w, precision)
+    assert res.status == 0
+    lab = binding.segment(res.F, res.G, res.factor_k, g["k"], seed=0)
+    ref = np.asarray(g["labels"])
+    inl = ~w.data.outlier
+    acc = oseg.matched_accuracy(lab, w.data.labels)
+    print(f"{name} {precision}: GPU segmentation matched accuracy {acc:.4f} (oracle {g['matched_accuracy_vs_truth']:.4f})"
+          f"; same partition over the {int(inl.sum())} subspace columns: {oseg.same_partition(lab[inl], ref[inl])}")
+    assert oseg.same_partition(lab[inl], ref[inl])
+    if w.M.shape[1] <= 5000:
+        # the CPU routine on the same (GPU) estimate agrees too
+        cpu = oseg.segment(res.Z.cpu().numpy().astype(np.float64), g["k"], seed=0)
+        assert oseg.same_partition(lab[inl], cpu[inl])

@@ -374,8 +374,8 @@ def bench_gemm(args):
     for the whole batch: M = rank(M), N = n, K = m (1000 x 20000 x 1000 for
     the 1000 x 20000 workload).  Device time per launch from CUDA events
     around `steps` back-to-back launches (lrr_gemm_timing), as a fraction of
-    the measured bf16 peak (the split-TF32 product does three TF32 MMAs per
-    term: its algorithmic rate counts the float32 product's 2 M N K flops).
+    the measured bf16 peak (the split products do three MMAs per term: their
+    algorithmic rate counts the float32 product's 2 M N K flops).
     Also the command the tensor-pipe counters are captured from."""
     import torch
     from paper_1304_5583_gb300 import binding
@@ -383,7 +383,7 @@ def bench_gemm(args):
     torch.cuda.set_device(0)
     peaks, src = _peaks()
     out = {"shape": [M, N, K], "peak_source": src, "bf16_peak_tflops": peaks["bf16_tflops"]}
-    for kind in ("bf16", "3xtf32"):
+    for kind in ("bf16", "bf16x3", "3xtf32"):
         ms = binding.gemm_timing(kind, M, N, K, repeat=max(1, args.steps))
         tf = 2.0 * M * N * K / (ms / 1e3) / 1e12
         out[kind] = {"ms_per_launch": ms, "tflops": tf, "frac_of_bf16_peak": tf / peaks["bf16_tflops"]}

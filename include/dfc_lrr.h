@@ -61,7 +61,9 @@ typedef enum {
     LRR_PREC_F64 = 0,    /* every step in float64                                     */
     LRR_PREC_F32 = 1,    /* iteration in float32, one-time factor in float64          */
     LRR_PREC_MIXED = 2   /* bf16 tensor-core products with float32 accumulation in the
-                            iteration bulk, float32 refinement phase to convergence    */
+                            iteration bulk (split bf16: hi and lo parts of each
+                            float32 operand, three bf16 MMAs per product), float32
+                            refinement phase to convergence                           */
 } lrr_precision;
 
 typedef struct {
@@ -93,9 +95,13 @@ typedef struct {
                                    ||Z + Y2/mu||_F > mixed_switch / mu, i.e. just before
                                    its SVT first keeps a direction (0 -> 0.5)            */
     int32_t profile;            /* 1: record per-phase CUDA-event times into stats     */
-    int32_t simt_products;      /* F32/MIXED: 1 = the float32 products of the iteration on
-                                   the CUDA cores; 0 (default) = on the tensor cores in
-                                   split TF32 (float32-accurate, see lrr_gemm_f32)      */
+    int32_t tc_products;        /* F32/MIXED: 1 = the float32 products of the iteration on
+                                   the tensor cores in split TF32 (each product float32-
+                                   accurate, see lrr_gemm_f32); 0 (default) = on the CUDA
+                                   cores.  Over a whole solve the split-TF32 iterate drifts
+                                   further from the float64 oracle (3.1e-5 against 1.5e-6
+                                   relative in block 1 of the 1000 x 20000 workload), so
+                                   it is not the default                                 */
     int32_t autotune;           /* 1: pick the launch shapes of the Jacobi and of the
                                    products by timing the candidates on the first solve
                                    of each problem shape (cached per process and device);
@@ -264,8 +270,9 @@ LRR_API int lrr_gemm_f32(const float* A, int64_t lda, const float* B, int64_t ld
 
 /* Device time of the iteration's tensor-core product alone, for measuring
  * it: kind 0 = the bf16 product (lrr_gemm_bf16), kind 1 = the split-TF32
- * product (lrr_gemm_f32) on operands already split.  Fills synthetic M x K
- * and K x N operands in scratch taken with cudaMallocAsync, launches the
+ * product (lrr_gemm_f32) on operands already split, kind 2 = the split-bf16
+ * product of the mixed form's bf16 phase (three bf16 MMAs, operands already
+ * split).  Fills synthetic M x K and K x N operands in scratch taken with cudaMallocAsync, launches the
  * kernel once untimed and `repeat` times back to back between two CUDA
  * events on `stream`, and stores the mean time per launch (ms). */
 LRR_API int lrr_gemm_timing(int32_t kind, int64_t M, int64_t N, int64_t K, int32_t repeat, double* ms_per_launch,

@@ -39,7 +39,7 @@ class LrrOptions(ctypes.Structure):
                 ("mu_max", ctypes.c_double), ("eps", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("batched", ctypes.c_int32), ("jacobi_sweeps", ctypes.c_int32),
                 ("rank_tol", ctypes.c_double), ("mixed_switch", ctypes.c_double), ("profile", ctypes.c_int32),
-                ("simt_products", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+                ("tc_products", ctypes.c_int32), ("autotune", ctypes.c_int32)]
 
 NPHASE = 12
 PHASES = ("setup", "gram", "warm", "jacobi", "svt_apply", "zgemm", "zupdate", "mzgemm", "eupdate", "stop",
@@ -181,7 +181,7 @@ def leading_dim(x):
 
 def options(lam: float, rho: float = 1.1, mu0: float = 1e-6, mu_max: float = 1e10, eps: float = 1e-6,
             max_iter: int = 1000, precision: str = "f32", batched: bool = True, jacobi_sweeps: int = 0,
-            rank_tol: float = 0.0, mixed_switch: float = 0.0, profile: bool = False, simt_products: bool = False,
+            rank_tol: float = 0.0, mixed_switch: float = 0.0, profile: bool = False, tc_products: bool = False,
             autotune: bool = False) -> LrrOptions:
     o = LrrOptions()
     load().lrr_default_options(ctypes.byref(o))
@@ -189,7 +189,7 @@ def options(lam: float, rho: float = 1.1, mu0: float = 1e-6, mu_max: float = 1e1
     o.max_iter, o.precision, o.batched = int(max_iter), PRECISIONS[precision], int(bool(batched))
     o.jacobi_sweeps, o.rank_tol, o.mixed_switch = int(jacobi_sweeps), float(rank_tol), float(mixed_switch)
     o.profile = int(bool(profile))
-    o.simt_products, o.autotune = int(bool(simt_products)), int(bool(autotune))
+    o.tc_products, o.autotune = int(bool(tc_products)), int(bool(autotune))
     return o
 
 
@@ -432,11 +432,12 @@ def unrolled_lrr(M, lam, K: int, mu0: float = 1e-6, rho: float = 1.1, mu_max: fl
 
 
 def gemm_timing(kind: str, M: int, N: int, K: int, repeat: int = 20) -> float:
-    """Mean device time (ms) of one launch of the bf16 ("bf16") or split-TF32
-    ("3xtf32") tensor-core product at M x N x K (lrr_gemm_timing)."""
+    """Mean device time (ms) of one launch of the bf16 ("bf16"), split-bf16
+    ("bf16x3") or split-TF32 ("3xtf32") tensor-core product at M x N x K
+    (lrr_gemm_timing)."""
     import torch
     ms = ctypes.c_double(0.0)
-    code = load().lrr_gemm_timing({"bf16": 0, "3xtf32": 1}[kind], M, N, K, repeat, ctypes.byref(ms),
+    code = load().lrr_gemm_timing({"bf16": 0, "3xtf32": 1, "bf16x3": 2}[kind], M, N, K, repeat, ctypes.byref(ms),
                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     if code < 0:
         raise LrrError(code)

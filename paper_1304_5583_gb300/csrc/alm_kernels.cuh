@@ -67,6 +67,14 @@ __global__ void fill_hash(T* __restrict__ x, int64_t count, uint32_t seed) {
     }
 }
 
+// split of x for the bf16x3 product: hi = x rounded to the nearest bf16,
+// lo = (x - hi) rounded to the nearest bf16 (x - hi is exact in float32)
+__device__ __forceinline__ void split_bf16(float x, uint16_t& hi, uint16_t& lo) {
+    const __nv_bfloat16 h = __float2bfloat16(x);
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(__float2bfloat16(x - __bfloat162float(h)));
+}
+
 // bf16 bit patterns of the same hashed values
 static __global__ void fill_hash_bf16(uint16_t* __restrict__ x, int64_t count, uint32_t seed) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
@@ -192,8 +200,8 @@ __global__ void z_update(int r, int64_t n, const int* __restrict__ colblk, const
                          const T* __restrict__ Theta, const T* __restrict__ Jt, T* __restrict__ Y2t,
                          T* __restrict__ Zt, T* __restrict__ D, T* __restrict__ A, const T* __restrict__ sig,
                          const T* __restrict__ dinv, T* __restrict__ dmax, double* __restrict__ afro,
-                         uint16_t* __restrict__ dbf, int64_t ldd, float* __restrict__ dhi,
-                         float* __restrict__ dlo, int64_t lds) {
+                         uint16_t* __restrict__ dbf, uint16_t* __restrict__ dbf_lo, int64_t ldd,
+                         float* __restrict__ dhi, float* __restrict__ dlo, int64_t lds) {
     const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= n) return;
@@ -213,7 +221,7 @@ __global__ void z_update(int r, int64_t n, const int* __restrict__ colblk, const
         const T av = z + y2n * imun;
         Zt[o + i] = z;
         Tt[o + i] = dl;
-        if (dbf) dbf[i + j * ldd] = __bfloat16_as_ushort(__float2bfloat16((float)dl));
+        if (dbf) split_bf16((float)dl, dbf[i + j * ldd], dbf_lo[i + j * ldd]);
         if (dhi) split_tf32((float)dl, dhi[i + j * lds], dlo[i + j * lds]);
         D[o + i] = dd;
         Y2t[o + i] = y2n;
@@ -236,8 +244,9 @@ template <typename T>
 __global__ void e_update(int64_t m, int64_t n, const int* __restrict__ colblk, const int* __restrict__ act,
                          const double* __restrict__ mu, double rho, double mu_max, double lam,
                          const T* __restrict__ Cp, const T* __restrict__ UD, T* __restrict__ Y1, T* __restrict__ E,
-                         T* __restrict__ Q, T* __restrict__ r1max, uint16_t* __restrict__ qbf, int64_t ldq,
-                         float* __restrict__ qhi, float* __restrict__ qlo, int64_t lds) {
+                         T* __restrict__ Q, T* __restrict__ r1max, uint16_t* __restrict__ qbf,
+                         uint16_t* __restrict__ qbf_lo, int64_t ldq, float* __restrict__ qhi,
+                         float* __restrict__ qlo, int64_t lds) {
     const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= n) return;
@@ -268,7 +277,7 @@ __global__ void e_update(int64_t m, int64_t n, const int* __restrict__ colblk, c
         Y1[o + i] = y1n;
         const T qv = y1n * imun - e;
         Q[o + i] = qv;
-        if (qbf) qbf[i + j * ldq] = __bfloat16_as_ushort(__float2bfloat16((float)qv));
+        if (qbf) split_bf16((float)qv, qbf[i + j * ldq], qbf_lo[i + j * ldq]);
         if (qhi) split_tf32((float)qv, qhi[i + j * lds], qlo[i + j * lds]);
         amax = fmax(amax, fabs(l1));
     }
@@ -409,6 +418,25 @@ __global__ void to_bf16_transposed(const T* __restrict__ src, int64_t ld, int64_
     for (int64_t i = blockIdx.y; i < rows; i += gridDim.y)
         for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols; j += (int64_t)gridDim.x * blockDim.x)
             dst[j + i * ldo] = __bfloat16_as_ushort(__float2bfloat16((float)src[i + j * ld]));
+}
+
+// split bf16 copies (hi, lo) of a column-major rows x cols matrix, same
+// orientation (as to_bf16_km)
+template <typename T>
+__global__ void to_bf16_split_km(const T* __restrict__ src, int64_t ld, int64_t rows, int64_t cols,
+                                 uint16_t* __restrict__ hi, uint16_t* __restrict__ lo, int64_t ldo) {
+    for (int64_t j = blockIdx.y; j < cols; j += gridDim.y)
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x)
+            split_bf16((float)src[i + j * ld], hi[i + j * ldo], lo[i + j * ldo]);
+}
+
+// split bf16 copies of the transpose (as to_bf16_transposed)
+template <typename T>
+__global__ void to_bf16_split_transposed(const T* __restrict__ src, int64_t ld, int64_t rows, int64_t cols,
+                                         uint16_t* __restrict__ hi, uint16_t* __restrict__ lo, int64_t ldo) {
+    for (int64_t i = blockIdx.y; i < rows; i += gridDim.y)
+        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cols; j += (int64_t)gridDim.x * blockDim.x)
+            split_bf16((float)src[i + j * ld], hi[j + i * ldo], lo[j + i * ldo]);
 }
 
 // split TF32 copy of a column-major rows x cols float32 matrix (same

@@ -71,10 +71,11 @@ struct OsjDesc {
 
 // One launch: every block is a thread-block cluster of `cluster` CTAs (0:
 // one per pivot of a round, up to osj_max_cluster()) that runs its sweeps
-// until converged or `sweeps` are done.
+// until converged or `sweeps` are done.  `quad_exit`: stop one sweep early
+// once quadratic convergence guarantees the tolerance (see osj_svd).
 template <typename T>
 cudaError_t osj_sweeps(const OsjDesc<T>* d_desc, int nmat, int max_pp, int sweeps, T tol, int* sweeps_run,
-                       cudaStream_t s, int cluster = 0);
+                       cudaStream_t s, int cluster = 0, int quad_exit = 0);
 // largest cluster size osj_sweeps uses on the current device (16 or 8)
 template <typename T>
 int osj_max_cluster();
@@ -94,13 +95,21 @@ cudaError_t tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb,
 
 // Float32-accurate product on the tensor cores (split TF32): C (M x N,
 // column-major, float) = A B from A = Ahi + Alo and B = Bhi + Blo, all four
-// float32, K-major, 16-byte aligned, lda and ldb multiples of 4, hi the TF32
-// truncation of the value and lo the float32 remainder (split_tf32 below).
+// float32, K-major, 16-byte aligned, lda and ldb multiples of 4, hi the
+// nearest TF32 value and lo the nearest TF32 value to the rest (split_tf32
+// below).
 // With flag != nullptr, 128-column tiles of C whose columns all belong to
 // blocks b (colblk) with flag[b] == 0 are left untouched.
 cudaError_t tc_gemm_3xtf32(const float* Ahi, const float* Alo, int64_t lda, const float* Bhi, const float* Blo,
                            int64_t ldb, float* C, int64_t ldc, int M, int N, int K, const int* colblk,
                            const int* flag, int* err, cudaStream_t s);
+
+// The same from split bf16 operands ("bf16x3"): A = Ahi + Alo, B = Bhi + Blo,
+// all four bf16, K-major, 16-byte aligned, lda and ldb multiples of 8, hi the
+// nearest bf16 value and lo the nearest bf16 value to the rest (split_bf16).
+// Relative error per product term about 2^-16, against 2^-8 for tc_gemm_bf16.
+cudaError_t tc_gemm_bf16x3(const void* Ahi, const void* Alo, int64_t lda, const void* Bhi, const void* Blo,
+                           int64_t ldb, float* C, int64_t ldc, int M, int N, int K, int* err, cudaStream_t s);
 
 // Split of x into hi + lo for the split-TF32 product: hi = x rounded to the
 // nearest TF32 value (10 explicit mantissa bits), lo = (x - hi) rounded to

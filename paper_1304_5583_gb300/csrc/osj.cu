@@ -296,9 +296,14 @@ __device__ T osj_pivot(const OsjDesc<T>& d, Smem<T>& sm, int a, int c) {
 // One cluster per matrix (blockIdx.y); the cluster's CTAs share the pivots of
 // each round.  `off` holds three slots per matrix (one per sweep, reused every
 // third sweep), `done` is set when the matrix converged.
+// With `quad_exit`, a sweep whose measure o (taken before its rotations)
+// satisfies 16 o^2 <= tol ends the loop without a confirming sweep: cyclic
+// Jacobi converges quadratically near the end (the off-diagonal part after a
+// sweep is O(o^2)), so the rotations of that sweep already bring the matrix
+// below the tolerance.
 template <typename T>
 __global__ void __launch_bounds__(NT, 5) osj_svd(const OsjDesc<T>* __restrict__ descs, int sweeps, T tol,
-                                              int* __restrict__ sweeps_run) {
+                                              int* __restrict__ sweeps_run, int quad_exit) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<T>& sm = *reinterpret_cast<Smem<T>*>(smem_raw);
     const int mat = blockIdx.y;
@@ -332,7 +337,7 @@ __global__ void __launch_bounds__(NT, 5) osj_svd(const OsjDesc<T>* __restrict__ 
         cl.sync();
         const T o = __ldcg(d.off + sw % 3);
         if (rank == 0 && t == 0 && sweeps_run) sweeps_run[mat] += 1;
-        if (o <= t_eff) {
+        if (o <= t_eff || (quad_exit && T(16) * o * o <= t_eff)) {
             if (rank == 0 && t == 0) *d.done = 1;
             break;
         }
@@ -398,7 +403,7 @@ int default_cluster(int nmat, int max_pairs, int cmax, size_t smem) {
 
 template <typename T>
 cudaError_t osj_sweeps(const OsjDesc<T>* d_desc, int nmat, int max_pp, int sweeps, T tol, int* sweeps_run,
-                       cudaStream_t s, int cluster) {
+                       cudaStream_t s, int cluster, int quad_exit) {
     if (nmat <= 0 || max_pp <= 0 || sweeps <= 0) return cudaSuccess;
     const int max_pairs = max_pp / B2;
     const size_t smem = sizeof(Smem<T>);
@@ -426,13 +431,13 @@ cudaError_t osj_sweeps(const OsjDesc<T>* d_desc, int nmat, int max_pp, int sweep
     at.val.clusterDim.x = (unsigned)csize; at.val.clusterDim.y = 1; at.val.clusterDim.z = 1;
     cfg.attrs = &at;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, osj_svd<T>, d_desc, sweeps, tol, sweeps_run);
+    e = cudaLaunchKernelEx(&cfg, osj_svd<T>, d_desc, sweeps, tol, sweeps_run, quad_exit);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-template cudaError_t osj_sweeps<float>(const OsjDesc<float>*, int, int, int, float, int*, cudaStream_t, int);
-template cudaError_t osj_sweeps<double>(const OsjDesc<double>*, int, int, int, double, int*, cudaStream_t, int);
+template cudaError_t osj_sweeps<float>(const OsjDesc<float>*, int, int, int, float, int*, cudaStream_t, int, int);
+template cudaError_t osj_sweeps<double>(const OsjDesc<double>*, int, int, int, double, int*, cudaStream_t, int, int);
 template int osj_max_cluster<float>();
 template int osj_max_cluster<double>();
 

@@ -114,9 +114,10 @@ struct Buffers {
     T** Hp;
     T** T1p;
     int *pv, *ppv;
-    // mixed precision: bf16 K-major operands of the tensor-core products
+    // mixed precision: split bf16 (hi, lo) K-major operands of the
+    // tensor-core products
     int64_t ldm8, ldr8;
-    uint16_t *Ubf, *USbf, *Pbf, *Zbf;
+    uint16_t *Ubf, *USbf, *Pbf, *Zbf, *Ubf_lo, *USbf_lo, *Pbf_lo, *Zbf_lo;
     int *fp32_on, *gemm32, *tc_err;
     // float32 products on the tensor cores (split TF32): U and U^T split once,
     // P = Y1/mu - E and Delta split by the kernels that produce them
@@ -236,6 +237,10 @@ Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector
     b.USbf = mixed ? a.take<uint16_t>(m * b.ldr8) : nullptr;
     b.Pbf = mixed ? a.take<uint16_t>(n * b.ldm8) : nullptr;
     b.Zbf = mixed ? a.take<uint16_t>(n * b.ldr8) : nullptr;
+    b.Ubf_lo = mixed ? a.take<uint16_t>(r * b.ldm8) : nullptr;
+    b.USbf_lo = mixed ? a.take<uint16_t>(m * b.ldr8) : nullptr;
+    b.Pbf_lo = mixed ? a.take<uint16_t>(n * b.ldm8) : nullptr;
+    b.Zbf_lo = mixed ? a.take<uint16_t>(n * b.ldr8) : nullptr;
     b.m4 = (m + 3) / 4 * 4;
     b.r4 = (r + 3) / 4 * 4;
     b.Uh = tc32 ? a.take<float>(b.m4 * r) : nullptr;
@@ -362,7 +367,7 @@ constexpr T jtol_of() { return sizeof(T) == 8 ? T(1e-13) : T(2e-6); }
 
 template <typename T>
 bool use_tc32(const lrr_problem* p, const lrr_options* o) {
-    return std::is_same<T, float>::value && o->precision != LRR_PREC_F64 && !o->simt_products && p->n <= kTcMaxN;
+    return std::is_same<T, float>::value && o->precision != LRR_PREC_F64 && o->tc_products && p->n <= kTcMaxN;
 }
 
 template <typename T, typename Tin>
@@ -471,9 +476,10 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     k::setup_factors<<<dim3(grid1(m), (unsigned)r), 256, 0, s>>>(B.Wd, B.mpp, m, r, B.order, B.lam, B.Ud, B.Usd);
     k::setup_scalars<T><<<dim3(grid1(m), (unsigned)r), 256, 0, s>>>(B.lam, r, B.Ud, m, B.sig, B.dinv, B.U, B.US);
     if (mixed) {
-        k::to_bf16_km<T><<<dim3(grid1(B.ldm8), (unsigned)r), 256, 0, s>>>(B.U, m, m, r, B.Ubf, B.ldm8);
-        k::to_bf16_transposed<T><<<dim3(grid1(B.ldr8), (unsigned)std::min<int64_t>(m, 65535)), 256, 0, s>>>(
-            B.U, m, m, r, B.USbf, B.ldr8);
+        k::to_bf16_split_km<T><<<dim3(grid1(B.ldm8), (unsigned)r), 256, 0, s>>>(B.U, m, m, r, B.Ubf, B.Ubf_lo,
+                                                                               B.ldm8);
+        k::to_bf16_split_transposed<T><<<dim3(grid1(B.ldr8), (unsigned)std::min<int64_t>(m, 65535)), 256, 0, s>>>(
+            B.U, m, m, r, B.USbf, B.USbf_lo, B.ldr8);
     }
     if constexpr (std::is_same<T, float>::value) {
         if (tc32) {
@@ -552,6 +558,9 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         j.strict = (dfc && t > 1 && i == 0) ? 1 : 0;
     }
     LRR_CUDA_TRY(cudaMemcpyAsync(B.jd, jdh.data(), sizeof(OsjDesc<T>) * t, cudaMemcpyHostToDevice, s));
+    // the float32 Jacobi stops without its confirming sweep once quadratic
+    // convergence guarantees the tolerance; float64 keeps the confirming sweep
+    const int quad_exit = sizeof(T) == 4 ? 1 : 0;
 
     // ---- autotune the Jacobi's cluster size (before the state is initialised:
     //      it runs on synthetic columns in the SVT buffers, then clears them)
@@ -585,7 +594,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
                     k::init_padded<T><<<grid1((int64_t)ppv[i] * ppv[i]), 256, 0, s>>>(B.W[i], pv[i], ppv[i], T(1), 1);
                 k::col_norm_max<T><<<t, 256, 0, s>>>(B.jd, B.svt_on, B.jscale, t);
                 cudaEventRecord(ta, s);
-                const cudaError_t e = osj_sweeps<T>(B.jd, t, max_pp, 2, jtol_of<T>(), nullptr, s, c);
+                const cudaError_t e = osj_sweeps<T>(B.jd, t, max_pp, 2, jtol_of<T>(), nullptr, s, c, quad_exit);
                 cudaEventRecord(tb, s);
                 if (e != cudaSuccess || cudaEventSynchronize(tb) != cudaSuccess) {
                     cudaEventDestroy(ta); cudaEventDestroy(tb);
@@ -684,6 +693,8 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         if (mixed) {
             LRR_CUDA_TRY(cudaMemsetAsync(B.Pbf, 0, sizeof(uint16_t) * n * B.ldm8, s));
             LRR_CUDA_TRY(cudaMemsetAsync(B.Zbf, 0, sizeof(uint16_t) * n * B.ldr8, s));
+            LRR_CUDA_TRY(cudaMemsetAsync(B.Pbf_lo, 0, sizeof(uint16_t) * n * B.ldm8, s));
+            LRR_CUDA_TRY(cudaMemsetAsync(B.Zbf_lo, 0, sizeof(uint16_t) * n * B.ldr8, s));
         }
     }
     for (int i = 0; i < t; ++i)   // the SVT reconstruction reads it with zero weights before the first SVD
@@ -726,7 +737,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         prof.end(LRR_PH_GRAM, 1 + nl(S_XT) + nl(S_XW));
         prof.begin();
         k::col_norm_max<T><<<t, 256, 0, s>>>(B.jd, B.svt_on, B.jscale, t);
-        LRR_CUDA_TRY(osj_sweeps<T>(B.jd, t, max_pp, sweeps, jtol, B.jsweeps, s, jcluster));
+        LRR_CUDA_TRY(osj_sweeps<T>(B.jd, t, max_pp, sweeps, jtol, B.jsweeps, s, jcluster, quad_exit));
         prof.end(LRR_PH_JACOBI, jac_launches + 1);
         prof.begin();
         k::svt_weights<T><<<t, 256, 0, s>>>(B.jd, B.hp, B.act, B.svt_on, B.mu, B.rank_cur, t);
@@ -741,7 +752,8 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         if constexpr (std::is_same<T, float>::value) {
             if (bf16_phase) {
                 // all columns at once; blocks already in float32 are recomputed below
-                LRR_CUDA_TRY(tc_gemm_bf16(B.Ubf, B.ldm8, B.Pbf, B.ldm8, B.Tt, r, r, (int)n, (int)m, B.tc_err, s));
+                LRR_CUDA_TRY(tc_gemm_bf16x3(B.Ubf, B.Ubf_lo, B.ldm8, B.Pbf, B.Pbf_lo, B.ldm8, B.Tt, r, r, (int)n,
+                                            (int)m, B.tc_err, s));
             }
         }
         if (tc32) {
@@ -755,14 +767,15 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         prof.begin();
         k::z_update<T><<<wgrid_n, 256, 0, s>>>(r, n, B.colblk, B.act, B.mu, o->rho, o->mu_max, B.Tt, B.Theta, B.Jt,
                                                B.Y2t, B.Zt, B.D, B.A, B.sig, B.dinv, B.dmax, B.afro,
-                                               bf16_phase ? B.Zbf : nullptr, B.ldr8, tc32 ? B.Dh : nullptr,
+                                               bf16_phase ? B.Zbf : nullptr, B.Zbf_lo, B.ldr8, tc32 ? B.Dh : nullptr,
                                                tc32 ? B.Dl : nullptr, B.r4);
         prof.end(LRR_PH_ZUPDATE, 1);
         // E-step, residuals, duals
         prof.begin();
         if constexpr (std::is_same<T, float>::value) {
             if (bf16_phase)
-                LRR_CUDA_TRY(tc_gemm_bf16(B.USbf, B.ldr8, B.Zbf, B.ldr8, B.MZ, m, (int)m, (int)n, r, B.tc_err, s));
+                LRR_CUDA_TRY(tc_gemm_bf16x3(B.USbf, B.USbf_lo, B.ldr8, B.Zbf, B.Zbf_lo, B.ldr8, B.MZ, m, (int)m,
+                                            (int)n, r, B.tc_err, s));
         }
         if (tc32) {
             LRR_CUDA_TRY(tc_gemm_3xtf32(B.UTh, B.UTl, B.r4, B.Dh, B.Dl, B.r4, reinterpret_cast<float*>(B.MZ), m,
@@ -774,7 +787,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         prof.begin();
         k::e_update<T><<<wgrid_n, 256, 0, s>>>(m, n, B.colblk, B.act, B.mu, o->rho, o->mu_max, o->lambda,
                                                has_perp ? B.C : nullptr, B.MZ, B.Y1, B.E, B.P, B.r1,
-                                               bf16_phase ? B.Pbf : nullptr, B.ldm8, tc32 ? B.Ph : nullptr,
+                                               bf16_phase ? B.Pbf : nullptr, B.Pbf_lo, B.ldm8, tc32 ? B.Ph : nullptr,
                                                tc32 ? B.Pl : nullptr, B.m4);
         prof.end(LRR_PH_EUPDATE, 1);
         prof.begin();
@@ -1533,12 +1546,13 @@ int lrr_gemm_f32(const float* A, int64_t lda, const float* B, int64_t ldb, float
 
 int lrr_gemm_timing(int32_t kind, int64_t M, int64_t N, int64_t K, int32_t repeat, double* ms_per_launch,
                     void* stream) {
-    if (!ms_per_launch || M < 1 || N < 1 || K < 1 || repeat < 1 || (kind != 0 && kind != 1)) return LRR_ERR_INVALID;
+    if (!ms_per_launch || M < 1 || N < 1 || K < 1 || repeat < 1 || kind < 0 || kind > 2) return LRR_ERR_INVALID;
     if (M > (1 << 20) || N > lrr::kTcMaxN || K > (1 << 20)) return LRR_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int64_t kp = kind == 0 ? (K + 7) / 8 * 8 : (K + 3) / 4 * 4;
-    const size_t esz = kind == 0 ? 2 : 4;
-    const size_t nops = kind == 0 ? 1 : 2;          // split TF32: hi and lo
+    const bool bf = kind != 1;
+    const int64_t kp = bf ? (K + 7) / 8 * 8 : (K + 3) / 4 * 4;
+    const size_t esz = bf ? 2 : 4;
+    const size_t nops = kind == 0 ? 1 : 2;          // split forms: hi and lo
     const size_t abytes = ((size_t)kp * M * esz + 255) / 256 * 256, bbytes = ((size_t)kp * N * esz + 255) / 256 * 256;
     const size_t total = nops * (abytes + bbytes) + sizeof(float) * (size_t)M * N + 256;
     void* mem = nullptr;
@@ -1555,6 +1569,11 @@ int lrr_gemm_timing(int32_t kind, int64_t M, int64_t N, int64_t K, int32_t repea
     if (kind == 0) {
         lrr::k::fill_hash_bf16<<<lrr::grid1(kp * M), 256, 0, s>>>(static_cast<uint16_t*>(A0), kp * M, 1u);
         lrr::k::fill_hash_bf16<<<lrr::grid1(kp * N), 256, 0, s>>>(static_cast<uint16_t*>(B0), kp * N, 2u);
+    } else if (kind == 2) {
+        lrr::k::fill_hash_bf16<<<lrr::grid1(kp * M), 256, 0, s>>>(static_cast<uint16_t*>(A0), kp * M, 1u);
+        lrr::k::fill_hash_bf16<<<lrr::grid1(kp * M), 256, 0, s>>>(static_cast<uint16_t*>(A1), kp * M, 3u);
+        lrr::k::fill_hash_bf16<<<lrr::grid1(kp * N), 256, 0, s>>>(static_cast<uint16_t*>(B0), kp * N, 2u);
+        lrr::k::fill_hash_bf16<<<lrr::grid1(kp * N), 256, 0, s>>>(static_cast<uint16_t*>(B1), kp * N, 4u);
     } else {
         lrr::k::fill_hash<float><<<lrr::grid1(kp * M), 256, 0, s>>>(static_cast<float*>(A0), kp * M, 1u);
         lrr::k::fill_hash<float><<<lrr::grid1(kp * M), 256, 0, s>>>(static_cast<float*>(A1), kp * M, 3u);
@@ -1562,6 +1581,7 @@ int lrr_gemm_timing(int32_t kind, int64_t M, int64_t N, int64_t K, int32_t repea
         lrr::k::fill_hash<float><<<lrr::grid1(kp * N), 256, 0, s>>>(static_cast<float*>(B1), kp * N, 4u);
     }
     auto launch = [&]() {
+        if (kind == 2) return lrr::tc_gemm_bf16x3(A0, A1, kp, B0, B1, kp, C, M, (int)M, (int)N, (int)K, err, s);
         return kind == 0 ? lrr::tc_gemm_bf16(A0, kp, B0, kp, C, M, (int)M, (int)N, (int)K, err, s)
                          : lrr::tc_gemm_3xtf32(static_cast<float*>(A0), static_cast<float*>(A1), kp,
                                                static_cast<float*>(B0), static_cast<float*>(B1), kp, C, M, (int)M,

@@ -253,15 +253,23 @@ __global__ void __launch_bounds__(NT, 1) tc_gemm_kernel(const __grid_constant__ 
 }
 
 // ---------------------------------------------------------------------------
-// Float32-accurate product on the tensor cores by split TF32 ("3xTF32"): every
-// float32 operand x is given as x ~ hi + lo, both exact TF32 values (hi the
-// nearest TF32 value to x, lo the nearest to x - hi; split_tf32); then
-//   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi     (+ a_lo b_lo, dropped)
-// run as kind::tf32 MMAs into one float32 accumulator.  The dropped term is
-// below 2^-22 |a b| and the split error below 2^-21 |a b|, both of random sign.
+// Float32-accurate products on the tensor cores from split operands: every
+// float32 operand x is given as x ~ hi + lo, hi and lo both exact in the
+// tensor-core input type (hi the nearest value to x, lo the nearest to x - hi),
+// and
+//   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi     (a_lo b_lo dropped)
+// runs as three MMAs into one float32 accumulator.
+//   split TF32 ("3xTF32", kind::tf32): the dropped term is below 2^-22 |a b|
+//     and the split error below 2^-21 |a b| (split_tf32);
+//   split bf16 ("bf16x3", the three-product form of Henry, Tang and Heinecke,
+//     "Leveraging the bfloat16 artificial intelligence datatype for
+//     higher-precision computations", ARITH 2019; kind::f16): hi and lo carry
+//     8 significant bits each, so the dropped term is below 2^-16 |a b| and
+//     the split error below 2^-17 |a b| -- about 2^7 below the bf16 product.
 // Same CTA structure as tc_gemm_kernel; a stage holds A_hi, A_lo, B_hi, B_lo
-// slabs of 32 float32 (128 bytes) along K.  With `tile_flag` set, a 128-column
-// tile whose columns all belong to blocks whose flag is zero is skipped.
+// slabs of 128 bytes along K (32 float32 or 64 bf16 values).  With
+// `tile_flag` set, a 128-column tile whose columns all belong to blocks whose
+// flag is zero is skipped.
 constexpr int BK32 = 32, STAGES32 = 3;
 constexpr uint32_t STAGE_BYTES32 = 4 * TILE_BYTES;
 
@@ -288,7 +296,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // the previous one.
 constexpr int SLAB = 2;
 
-__global__ void __launch_bounds__(NT, 1) tc_gemm_3xtf32_kernel(
+template <bool BF>
+__global__ void __launch_bounds__(NT, 1) tc_gemm_split_kernel(
     const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
     const __grid_constant__ CUtensorMap mapBh, const __grid_constant__ CUtensorMap mapBl, float* __restrict__ C,
     int64_t ldc, int M, int N, int K, int* __restrict__ err, const TileSkip sk) {
@@ -300,7 +309,8 @@ __global__ void __launch_bounds__(NT, 1) tc_gemm_3xtf32_kernel(
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    const int nk = (K + BK32 - 1) / BK32;
+    constexpr int KB = BF ? BK : BK32;           // K values per 128-byte slab
+    const int nk = (K + KB - 1) / KB;
     const int nslab = (nk + SLAB - 1) / SLAB;
 
     // leave (uniformly, before any barrier or TMEM use) when no column of
@@ -347,10 +357,10 @@ __global__ void __launch_bounds__(NT, 1) tc_gemm_3xtf32_kernel(
                 if (abort_flag) break;
                 unsigned char* st = base + s * STAGE_BYTES32;
                 mbar_expect_tx(&full_bar[s], STAGE_BYTES32);
-                tma_load_2d(st, &mapAh, kb * BK32, m0, &full_bar[s]);
-                tma_load_2d(st + TILE_BYTES, &mapAl, kb * BK32, m0, &full_bar[s]);
-                tma_load_2d(st + 2 * TILE_BYTES, &mapBh, kb * BK32, n0, &full_bar[s]);
-                tma_load_2d(st + 3 * TILE_BYTES, &mapBl, kb * BK32, n0, &full_bar[s]);
+                tma_load_2d(st, &mapAh, kb * KB, m0, &full_bar[s]);
+                tma_load_2d(st + TILE_BYTES, &mapAl, kb * KB, m0, &full_bar[s]);
+                tma_load_2d(st + 2 * TILE_BYTES, &mapBh, kb * KB, n0, &full_bar[s]);
+                tma_load_2d(st + 3 * TILE_BYTES, &mapBl, kb * KB, n0, &full_bar[s]);
                 issued = kb + 1;
             }
             if (abort_flag) {
@@ -360,7 +370,7 @@ __global__ void __launch_bounds__(NT, 1) tc_gemm_3xtf32_kernel(
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_tf32(BM, BN);
+            constexpr uint32_t idesc = BF ? idesc_bf16(BM, BN) : idesc_tf32(BM, BN);
             bool ok = true;
             for (int kb = 0; kb < nk && ok; ++kb) {
                 const int s = kb % STAGES32;
@@ -374,22 +384,31 @@ __global__ void __launch_bounds__(NT, 1) tc_gemm_3xtf32_kernel(
                 const uint32_t ah = smem_u32(base + s * STAGE_BYTES32);
                 const uint32_t al = ah + TILE_BYTES, bh = ah + 2 * TILE_BYTES, bl = ah + 3 * TILE_BYTES;
 #pragma unroll
-                for (int k = 0; k < BK32 / 8; ++k) {
-                    const uint32_t off = k * 32;    // 8 float32 along K
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t off = k * 32;    // 32 bytes along K: 8 float32 or 16 bf16
                     const uint64_t dah = smem_desc(ah + off), dal = smem_desc(al + off);
                     const uint64_t dbh = smem_desc(bh + off), dbl = smem_desc(bl + off);
                     const uint32_t accum = (in_slab > 0 || k > 0) ? 1u : 0u;
                     // small terms first, the hi x hi term last
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
-                        "l"(dal), "l"(dbh), "r"(idesc), "r"(accum));
-                    asm volatile(
-                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(acc), "l"(dah), "l"(dbl),
-                        "r"(idesc));
-                    asm volatile(
-                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(acc), "l"(dah), "l"(dbh),
-                        "r"(idesc));
+                    if constexpr (BF) {
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
+                            "l"(dal), "l"(dbh), "r"(idesc), "r"(accum));
+                        asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 1;\n" ::"r"(acc),
+                                     "l"(dah), "l"(dbl), "r"(idesc));
+                        asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 1;\n" ::"r"(acc),
+                                     "l"(dah), "l"(dbh), "r"(idesc));
+                    } else {
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
+                            "l"(dal), "l"(dbh), "r"(idesc), "r"(accum));
+                        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(acc),
+                                     "l"(dah), "l"(dbl), "r"(idesc));
+                        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(acc),
+                                     "l"(dah), "l"(dbh), "r"(idesc));
+                    }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                                  smem_u32(&empty_bar[s]))
@@ -510,26 +529,41 @@ cudaError_t tc_launch(const void* A, int64_t lda, const void* B, int64_t ldb, fl
 }
 }  // namespace
 
-cudaError_t tc_gemm_3xtf32(const float* Ahi, const float* Alo, int64_t lda, const float* Bhi, const float* Blo,
-                           int64_t ldb, float* C, int64_t ldc, int M, int N, int K, const int* colblk,
-                           const int* flag, int* err, cudaStream_t s) {
+namespace {
+template <bool BF>
+cudaError_t split_launch(const void* Ahi, const void* Alo, int64_t lda, const void* Bhi, const void* Blo, int64_t ldb,
+                         float* C, int64_t ldc, int M, int N, int K, const int* colblk, const int* flag, int* err,
+                         cudaStream_t s) {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-    if ((lda % 4) || (ldb % 4)) return cudaErrorInvalidValue;
-    for (const void* p : {(const void*)Ahi, (const void*)Alo, (const void*)Bhi, (const void*)Blo})
+    const int64_t align = BF ? 8 : 4;               // 16-byte row strides
+    if ((lda % align) || (ldb % align)) return cudaErrorInvalidValue;
+    for (const void* p : {Ahi, Alo, Bhi, Blo})
         if (reinterpret_cast<uintptr_t>(p) % 16) return cudaErrorInvalidValue;
     if (flag && !colblk) return cudaErrorInvalidValue;
     CUtensorMap mah, mal, mbh, mbl;
-    if (!make_map(&mah, Ahi, K, M, lda, true) || !make_map(&mal, Alo, K, M, lda, true) ||
-        !make_map(&mbh, Bhi, K, N, ldb, true) || !make_map(&mbl, Blo, K, N, ldb, true))
+    if (!make_map(&mah, Ahi, K, M, lda, !BF) || !make_map(&mal, Alo, K, M, lda, !BF) ||
+        !make_map(&mbh, Bhi, K, N, ldb, !BF) || !make_map(&mbl, Blo, K, N, ldb, !BF))
         return cudaErrorInvalidValue;
     if (ceil_div(N, BN) > 65535) return cudaErrorInvalidValue;
     const size_t smem = (size_t)STAGES32 * STAGE_BYTES32 + 1024;
     static std::atomic<uint64_t> smem_set{0};
-    const cudaError_t ea = ensure_smem_limit(tc_gemm_3xtf32_kernel, (int)smem, smem_set);
+    const cudaError_t ea = ensure_smem_limit(tc_gemm_split_kernel<BF>, (int)smem, smem_set);
     if (ea != cudaSuccess) return ea;
     const dim3 grid((unsigned)ceil_div(M, BM), (unsigned)ceil_div(N, BN));
-    tc_gemm_3xtf32_kernel<<<grid, NT, smem, s>>>(mah, mal, mbh, mbl, C, ldc, M, N, K, err, TileSkip{colblk, flag});
+    tc_gemm_split_kernel<BF><<<grid, NT, smem, s>>>(mah, mal, mbh, mbl, C, ldc, M, N, K, err, TileSkip{colblk, flag});
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t tc_gemm_3xtf32(const float* Ahi, const float* Alo, int64_t lda, const float* Bhi, const float* Blo,
+                           int64_t ldb, float* C, int64_t ldc, int M, int N, int K, const int* colblk,
+                           const int* flag, int* err, cudaStream_t s) {
+    return split_launch<false>(Ahi, Alo, lda, Bhi, Blo, ldb, C, ldc, M, N, K, colblk, flag, err, s);
+}
+
+cudaError_t tc_gemm_bf16x3(const void* Ahi, const void* Alo, int64_t lda, const void* Bhi, const void* Blo,
+                           int64_t ldb, float* C, int64_t ldc, int M, int N, int K, int* err, cudaStream_t s) {
+    return split_launch<true>(Ahi, Alo, lda, Bhi, Blo, ldb, C, ldc, M, N, K, nullptr, nullptr, err, s);
 }
 
 cudaError_t tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int M, int N,

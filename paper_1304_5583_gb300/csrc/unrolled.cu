@@ -214,7 +214,6 @@ struct Engine {
     OsjDesc<T>* od;
     T *oscale, *ooff;
     int *odone, *oon;
-    double* omu;
     T **pW, **pH, **pT;
     int *pv, *ppv;
     GemmDesc<T>* gd;
@@ -271,7 +270,6 @@ size_t carve_engine(Engine<T>& g, Bump& b) {
     g.od = b.take<OsjDesc<T>>(1);
     g.oscale = b.take<T>(1); g.ooff = b.take<T>(3);
     g.odone = b.take<int>(1); g.oon = b.take<int>(1);
-    g.omu = b.take<double>(1);
     g.pW = b.take<T*>(1); g.pH = b.take<T*>(1); g.pT = b.take<T*>(1);
     g.pv = b.take<int>(1); g.ppv = b.take<int>(1);
     g.gd = b.take<GemmDesc<T>>(64);
@@ -398,7 +396,6 @@ int svt(Engine<T>& g, double mu, T* Uout, T* Vrout, T* Sout) {
     UTRY(g.gemm(false, false, (int)n, r, r, T(1), g.At, n, g.Wj, pp, T(0), g.X, n));
     const int one = 1;
     UTRY(cudaMemcpyAsync(g.oon, &one, sizeof(int), cudaMemcpyHostToDevice, s));
-    UTRY(cudaMemcpyAsync(g.omu, &mu, sizeof(double), cudaMemcpyHostToDevice, s));
     lrr::k::col_norm_max<T><<<1, 256, 0, s>>>(g.od, g.oon, g.oscale, 1);
     UTRY(osj_sweeps<T>(g.od, 1, pp, 40, sizeof(T) == 8 ? T(1e-13) : T(2e-6), nullptr, s, 0));
     const T tau = (T)(1.0 / mu);
@@ -567,7 +564,10 @@ template <typename T>
 int engine_init(Engine<T>& g) {
     cudaStream_t s = g.s;
     OsjDesc<T> d{};
-    d.X = g.X; d.W = g.Wj; d.done = g.odone; d.off = g.ooff; d.active = g.oon; d.scale = g.oscale; d.mu = g.omu;
+    d.X = g.X; d.W = g.Wj; d.done = g.odone; d.off = g.ooff; d.active = g.oon; d.scale = g.oscale;
+    // no threshold in the measure (d.mu null): the reverse pass needs every
+    // singular pair resolved, including the ones the SVT removes
+    d.mu = nullptr;
     d.ldx = g.n; d.ldw = g.pp; d.L = (int)g.n; d.p = g.r; d.pp = g.pp; d.strict = 1;
     UTRY(cudaMemcpyAsync(g.od, &d, sizeof(d), cudaMemcpyHostToDevice, s));
     T* ptrs[3] = {g.Wj, g.Wg, g.Wt};

@@ -249,17 +249,20 @@ def test_autotuned_launch_shape_gives_bitwise_identical_results(lib):
 
 
 @pytest.mark.parametrize("precision", ["f32", "mixed"])
-def test_cuda_core_products_match_oracle(lib, precision):
-    """The float32 products on the CUDA cores (simt_products) instead of split
-    TF32 on the tensor cores: same parity with the oracle."""
+def test_tensor_core_products_match_oracle(lib, precision):
+    """The float32 products on the tensor cores in split TF32 (tc_products)
+    instead of the CUDA cores: same parity with the oracle."""
     w = synth.workload("small_dfc_60x240")
-    res, M = _run(lib, w, precision, simt_products=True)
+    res, M = _run(lib, w, precision, tc_products=True)
     assert res.status == 0
     ref = olrr.dfc_lrr(M, w.perm, w.offsets, w.lam, eps=w.eps, max_iter=w.max_iter, fixed_iters=list(res.iters))
     assert _rel(res.Z.cpu().numpy(), ref.Z) < 1e-5
 
 
-@pytest.mark.parametrize("rank", [0, 40])
+# ranks at clear gaps of the combined block spectrum (0.9996 | 0.9931 and
+# 0.62 | 2e-6 on this workload); the default k1 = 12 falls between 1.00187 and
+# 1.00169, where the truncation's subspace is not determined to float32 precision
+@pytest.mark.parametrize("rank", [24, 36])
 def test_footnote_variant_matches_oracle(lib, rank):
     """Dictionary C_i per block (the footnote to eq. (2)), blocks solved as
     independent problems on concurrent streams, C step = truncated SVD of

@@ -69,7 +69,7 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -182,7 +182,8 @@ def bench_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     clocks = ClockSampler(dev.index)
-    clocks.start()
+    if not args.no_clocks:
+        clocks.start()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     try:
@@ -231,6 +232,26 @@ def bench_ours(args, rank, world):
     e2e_ms = f0.elapsed_time(f1) / e_steps
     h2d = Mh.nbytes
     d2h = Zh.numel() * Zh.element_size() + Sh.numel() * Sh.element_size()
+
+    # ---- the same with Z returned in factored form (Z = F[:, :k] G[:k], Section
+    #      2.2's low-rank output) instead of the dense n x n matrix
+    kmax = binding.factor_max_rank(Md, w.perm, w.offsets)
+    Fh = torch.empty((kmax, n), dtype=Md.dtype, pin_memory=True).t()
+    Gh = torch.empty((n, kmax), dtype=Md.dtype, pin_memory=True).t()
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(e_steps):
+        Mdev = torch.empty((n, m), dtype=Md.dtype, device=dev).t()
+        Mdev.copy_(Mpin, non_blocking=True)
+        rr = binding.dfc_lrr_solve(Mdev, w.perm, w.offsets, opts, workspace=ws, want_Z=False, want_factors=True)
+        Fh.copy_(rr.F, non_blocking=True)
+        Gh.copy_(rr.G, non_blocking=True)
+        Sh.copy_(rr.S, non_blocking=True)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    e2e_fact_ms = g0.elapsed_time(g1) / e_steps
+    d2h_fact = (Fh.numel() + Gh.numel() + Sh.numel()) * Sh.element_size()
 
     # ---- roofline of the dominant kernel family
     peaks, src = _peaks()
@@ -282,6 +303,8 @@ def bench_ours(args, rank, world):
         "svt": {"sweeps": res.stats["svt_sweeps"], "calls": res.stats["svt_calls"]},
         "roofline": roof,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "e2e_factored": {"value": e2e_fact_ms / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d),
+                         "d2h_bytes_per_step": int(d2h_fact), "k": int(rr.factor_k), "kmax": int(kmax)},
         "gpu_launches": launches * args.steps,
         "clocks": clk,
     }
@@ -406,6 +429,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="fixed launch shapes instead of the autotuner")
     ap.add_argument("--oracle-iters", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true",
+                    help="no nvidia-smi sampling (for runs under a profiler, which waits for child processes)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the float32 one-block-at-a-time comparison solve")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)

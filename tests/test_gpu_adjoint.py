@@ -86,6 +86,20 @@ def test_config_200x1000_gradient_against_central_differences(lib, precision):
     fd = np.array(g["fd_dM"])
     err = float(np.linalg.norm(got - fd) / np.linalg.norm(fd))
     errl = abs(lb - g["fd_dlam"]) / abs(g["fd_dlam"])
-    print(f"{precision}: 50 entries of dL/dM vs central differences {err:.2e}; dL/dlam {errl:.2e}")
-    tol = 1e-6 if precision == "f64" else 2e-3
-    assert err < tol and errl < tol
+    ora = np.array(g["oracle_dM"])
+    erro = float(np.linalg.norm(got - ora) / np.linalg.norm(ora))
+    print(f"{precision}: 50 entries of dL/dM vs central differences {err:.2e}, vs the oracle's reverse mode "
+          f"{erro:.2e}; dL/dlam {errl:.2e}")
+    # The central differences carry cancellation error: |L| eps / h ~ 1e-8 per
+    # entry against entries of 1e-4 .. 4e-3, so about 2e-5 relative over the 50
+    # entries (the oracle's own reverse mode is 2.1e-5 from them).  float64 is
+    # therefore held to the differences at 1e-4 and to the oracle's reverse mode
+    # (the same 30 iterations in float64) at 1e-8.  float32: the rounding of
+    # the forward iterates passes through the SVT derivative's 1/(s_i - s_j)
+    # factors 30 times; held at 1e-2.
+    if precision == "f64":
+        assert err < 1e-4 and errl < 1e-4
+        assert erro < 1e-8
+        assert abs(lb - g["oracle_dlam"]) <= 1e-8 * abs(g["oracle_dlam"])
+    else:
+        assert err < 1e-2 and errl < 1e-2

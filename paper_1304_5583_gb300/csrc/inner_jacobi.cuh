@@ -52,9 +52,13 @@ __device__ int inner_jacobi(T (*S)[LDS], T (*R)[LDS], T* cs, T* sn, int* pi, int
                 const T s_pu = S[p][u], s_pv = S[p][v], s_qu = S[q][u], s_qv = S[q][v];
                 const T r_pu = ck * s_pu - sk * s_qu, r_pv = ck * s_pv - sk * s_qv;
                 const T r_qu = sk * s_pu + ck * s_qu, r_qv = sk * s_pv + ck * s_qv;
+                // the rotated pair's own off-diagonal entries are zero by
+                // construction (k == l: u = p, v = q); only this thread
+                // touches them in this step
+                const bool own = k == l && sk != T(0);
                 S[p][u] = cl * r_pu - sl * r_pv;
-                S[p][v] = sl * r_pu + cl * r_pv;
-                S[q][u] = cl * r_qu - sl * r_qv;
+                S[p][v] = own ? T(0) : sl * r_pu + cl * r_pv;
+                S[q][u] = own ? T(0) : cl * r_qu - sl * r_qv;
                 S[q][v] = sl * r_qu + cl * r_qv;
             }
             // R <- R J
@@ -66,8 +70,6 @@ __device__ int inner_jacobi(T (*S)[LDS], T (*R)[LDS], T* cs, T* sn, int* pi, int
                 R[i][u] = cl * x - sl * y;
                 R[i][v] = sl * x + cl * y;
             }
-            __syncthreads();
-            if (t < b && sn[t] != T(0)) { S[pi[t]][qi[t]] = T(0); S[qi[t]][pi[t]] = T(0); }
             __syncthreads();
         }
         rotated_total |= rotated;

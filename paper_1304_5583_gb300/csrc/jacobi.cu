@@ -193,9 +193,11 @@ __global__ void jac_check(const JacDesc<T>* __restrict__ descs, int nmat, T tol)
 }  // namespace
 
 template <typename T>
-cudaError_t jacobi_sweeps(const JacDesc<T>* d_desc, int nmat, int max_pp, int sweeps, T tol, cudaStream_t s) {
+cudaError_t jacobi_sweeps(const JacDesc<T>* d_desc, int nmat, int max_pp, int sweeps, T tol, cudaStream_t s,
+                         const int* done_dev, int* sweeps_run) {
     constexpr int b = jacobi_bs<T>();
     constexpr int B2 = 2 * b;
+    if (sweeps_run) *sweeps_run = 0;
     if (nmat <= 0 || max_pp <= 0) return cudaSuccess;
     const int nb = max_pp / b, npairs = nb / 2;
     jac_reset<T><<<ceil_div(nmat, 128), 128, 0, s>>>(d_desc, nmat);
@@ -207,11 +209,22 @@ cudaError_t jacobi_sweeps(const JacDesc<T>* d_desc, int nmat, int max_pp, int sw
             jac_apply<T, B2><<<ga, NT, 0, s>>>(d_desc, r);
         }
         jac_check<T><<<ceil_div(nmat, 128), 128, 0, s>>>(d_desc, nmat, tol);
+        if (sweeps_run) *sweeps_run = sw + 1;
+        if (done_dev) {
+            // one matrix: stop launching once it has converged
+            int done = 0;
+            cudaError_t e = cudaMemcpyAsync(&done, done_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return e;
+            if (done) break;
+        }
     }
     return cudaGetLastError();
 }
 
-template cudaError_t jacobi_sweeps<float>(const JacDesc<float>*, int, int, int, float, cudaStream_t);
-template cudaError_t jacobi_sweeps<double>(const JacDesc<double>*, int, int, int, double, cudaStream_t);
+template cudaError_t jacobi_sweeps<float>(const JacDesc<float>*, int, int, int, float, cudaStream_t, const int*,
+                                          int*);
+template cudaError_t jacobi_sweeps<double>(const JacDesc<double>*, int, int, int, double, cudaStream_t, const int*,
+                                           int*);
 
 }  // namespace lrr

@@ -50,8 +50,12 @@ struct JacDesc {
 // pp/bs diagonal blocks) on every matrix; a matrix stops once a whole sweep
 // saw no scaled off-diagonal |G_ij|/sqrt(G_ii G_jj) above tol.  bs = 16 for
 // double, 32 for float.  `done` and `off` are reset at entry.
+// With done_dev (the `done` word of a single matrix) the host reads it after
+// every sweep and stops launching once it is set; sweeps_run (host) receives
+// the sweeps launched.
 template <typename T>
-cudaError_t jacobi_sweeps(const JacDesc<T>* d_desc, int nmat, int max_pp, int sweeps, T tol, cudaStream_t s);
+cudaError_t jacobi_sweeps(const JacDesc<T>* d_desc, int nmat, int max_pp, int sweeps, T tol, cudaStream_t s,
+                         const int* done_dev = nullptr, int* sweeps_run = nullptr);
 // One-sided block Jacobi (osj.cu): X (L x p, ld ldx) is rotated to orthogonal
 // columns together with W (p x p, ld ldw); pp = p rounded up to the pivot
 // width.  off points at three slots (the per-sweep convergence maxima).

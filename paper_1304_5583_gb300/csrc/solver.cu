@@ -88,6 +88,12 @@ struct Buffers {
     double *jac_off_d, *jac_scale_d;
     int *jac_done_d, *order;
     JacDesc<double>* jac_setup;
+    // float32 start of the factor: K and its eigenvectors in float32, then
+    // float64 scratch for the polish from that basis
+    float *Kf, *Wf, *Rf, *jac_off_f, *jac_scale_f;
+    int *rot_f, *jac_done_f;
+    JacDesc<float>* jac_setup_f;
+    double *T1d, *T2d;
     // factor in the iteration precision
     T *U, *US, *sig, *dinv, *V, *nu;
     // state (m x n) and reduced state (rmax x n)
@@ -142,8 +148,10 @@ Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector
     b.t = p->t;
     b.rmax = (int)std::min<int64_t>(p->m, p->n);
     constexpr int B2d = 2 * jacobi_bs<double>();
+    constexpr int B2f = 2 * jacobi_bs<float>();
+    static_assert(B2f % B2d == 0, "padding serves both precisions");
     constexpr int B2 = osj_pivot_width();
-    b.mpp = round_up((int)p->m, B2d);
+    b.mpp = round_up((int)p->m, B2f);
     const int64_t m = p->m, n = p->n, r = b.rmax, mpp = b.mpp;
     b.Md = need_md ? a.take<double>(m * n) : nullptr;
     b.Kd = a.take<double>(mpp * mpp);
@@ -159,6 +167,16 @@ Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector
     b.jac_scale_d = a.take<double>(1);
     b.jac_done_d = a.take<int>(1);
     b.jac_setup = a.take<JacDesc<double>>(1);
+    b.Kf = a.take<float>(mpp * mpp);
+    b.Wf = a.take<float>(mpp * mpp);
+    b.Rf = a.take<float>(mpp * B2f);
+    b.rot_f = a.take<int>(mpp / B2f);
+    b.jac_off_f = a.take<float>(1);
+    b.jac_scale_f = a.take<float>(1);
+    b.jac_done_f = a.take<int>(1);
+    b.jac_setup_f = a.take<JacDesc<float>>(1);
+    b.T1d = a.take<double>(mpp * mpp);
+    b.T2d = a.take<double>(mpp * mpp);
     b.U = a.take<T>(m * r);
     b.US = a.take<T>(m * r);
     b.sig = a.take<T>(r);
@@ -435,6 +453,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         Md = reinterpret_cast<const double*>(M);
     }
     std::vector<GemmDesc<double>> hd(3);
+    int setup_sweeps[2] = {0, 0};     // float32 and float64 Jacobi sweeps of the factor
     hd[0] = gdesc<double>(Md, ldmd, Md, ldmd, B.Kd, B.mpp, (int)m, (int)m, (int)n, nullptr);
     GemmDesc<double>* dd = reinterpret_cast<GemmDesc<double>*>(B.gd);  // scratch slot, reused below
     LRR_CUDA_TRY(cudaMemcpyAsync(dd, hd.data(), sizeof(GemmDesc<double>), cudaMemcpyHostToDevice, s));
@@ -450,12 +469,57 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         double sc = 0;
         for (double v : dg) sc = std::max(sc, std::fabs(v));
         if (!(sc > 0)) return LRR_ERR_RANK;
+        // The eigendecomposition starts in float32 and is finished in float64:
+        //   1. K_f = float(K), block Jacobi in float32 -> eigenvectors U0
+        //      (orthogonal to ~1e-6, the large eigenpairs already resolved);
+        //   2. U0 in float64, made orthonormal to float64 rounding by two
+        //      Newton-Schulz steps U0 <- U0 (3I - U0^T U0)/2 (quadratic from a
+        //      1e-6 defect);
+        //   3. K' = U0^T K U0 in float64 is nearly diagonal; the float64 block
+        //      Jacobi on K' converges in a few sweeps to K' = W diag(lambda) W^T;
+        //   4. the eigenvectors of K are U0 W.
+        // The float64 sweeps decide the accuracy (same tolerance as a float64
+        // start); the float32 start only removes the sweeps that float64 would
+        // spend on the large rotations.
+        const int64_t mp = B.mpp, mm = mp * mp;
+        k::copy_convert_f64<float><<<grid1(mm), 256, 0, s>>>(B.Kd, B.Kf, mm);
+        k::init_padded<float><<<grid1(mm), 256, 0, s>>>(B.Wf, (int)m, (int)mp, 1.f, 1);
+        const float scf = (float)sc;
+        JacDesc<float> jf{};
+        jf.G = B.Kf; jf.W = B.Wf; jf.R = B.Rf; jf.rot = B.rot_f; jf.done = B.jac_done_f; jf.off = B.jac_off_f;
+        jf.active = nullptr; jf.scale = B.jac_scale_f; jf.pp = (int)mp;
+        LRR_CUDA_TRY(cudaMemcpyAsync(B.jac_scale_f, &scf, sizeof(float), cudaMemcpyHostToDevice, s));
+        LRR_CUDA_TRY(cudaMemcpyAsync(B.jac_setup_f, &jf, sizeof(jf), cudaMemcpyHostToDevice, s));
+        LRR_CUDA_TRY(jacobi_sweeps<float>(B.jac_setup_f, 1, (int)mp, 40, 1e-5f, s, B.jac_done_f, &setup_sweeps[0]));
+        double* U0 = B.T2d;
+        double* G1 = B.T1d;
+        k::copy_convert_to_f64<float><<<grid1(mm), 256, 0, s>>>(B.Wf, U0, mm);
+        auto gemm1 = [&](const double* A, const double* Bm, double* C, bool ta, double alpha, double beta) {
+            GemmDesc<double> g = gdesc<double>(A, mp, Bm, mp, C, mp, (int)mp, (int)mp, (int)mp, nullptr, alpha, beta);
+            cudaError_t e = cudaMemcpyAsync(dd, &g, sizeof(g), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = gemm_grouped<double>(dd, 1, ta, false, (int)mp, (int)mp, s);
+            return e;
+        };
+        for (int it = 0; it < 2; ++it) {
+            // G1 = U0^T U0;  Wd = 1.5 U0 - 0.5 U0 G1;  U0 <- Wd
+            LRR_CUDA_TRY(gemm1(U0, U0, G1, true, 1.0, 0.0));
+            LRR_CUDA_TRY(cudaMemcpyAsync(B.Wd, U0, sizeof(double) * mm, cudaMemcpyDeviceToDevice, s));
+            LRR_CUDA_TRY(gemm1(U0, G1, B.Wd, false, -0.5, 1.5));
+            LRR_CUDA_TRY(cudaMemcpyAsync(U0, B.Wd, sizeof(double) * mm, cudaMemcpyDeviceToDevice, s));
+        }
+        // K' = U0^T (K U0), in place of K
+        LRR_CUDA_TRY(gemm1(B.Kd, U0, G1, false, 1.0, 0.0));
+        LRR_CUDA_TRY(gemm1(U0, G1, B.Kd, true, 1.0, 0.0));
+        k::init_padded<double><<<grid1(mm), 256, 0, s>>>(B.Wd, (int)m, (int)mp, 1.0, 1);
         JacDesc<double> jd{};
         jd.G = B.Kd; jd.W = B.Wd; jd.R = B.Rd; jd.rot = B.rot_d; jd.done = B.jac_done_d; jd.off = B.jac_off_d;
-        jd.active = nullptr; jd.scale = B.jac_scale_d; jd.pp = B.mpp;
+        jd.active = nullptr; jd.scale = B.jac_scale_d; jd.pp = (int)mp;
         LRR_CUDA_TRY(cudaMemcpyAsync(B.jac_scale_d, &sc, sizeof(double), cudaMemcpyHostToDevice, s));
         LRR_CUDA_TRY(cudaMemcpyAsync(B.jac_setup, &jd, sizeof(jd), cudaMemcpyHostToDevice, s));
-        LRR_CUDA_TRY(jacobi_sweeps<double>(B.jac_setup, 1, B.mpp, 40, 1e-13, s));
+        LRR_CUDA_TRY(jacobi_sweeps<double>(B.jac_setup, 1, (int)mp, 40, 1e-13, s, B.jac_done_d, &setup_sweeps[1]));
+        // eigenvectors of K: U0 W
+        LRR_CUDA_TRY(gemm1(U0, B.Wd, G1, false, 1.0, 0.0));
+        LRR_CUDA_TRY(cudaMemcpyAsync(B.Wd, G1, sizeof(double) * mm, cudaMemcpyDeviceToDevice, s));
     }
     k::diag_of<double><<<ceil_div(m, 256), 256, 0, s>>>(B.Kd, B.mpp, m, B.lam_raw);
     std::vector<double> ev_h((size_t)m);
@@ -521,8 +585,13 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
     LRR_CUDA_TRY(cudaStreamSynchronize(s));
     LRR_CUDA_TRY(cudaEventRecord(ev[1], s));
     {
-        const int64_t nbd = B.mpp / jacobi_bs<double>();
-        const int64_t setup_launches = 1 + (need_md ? 1 : 0) + 2 + 1 + 2 + (1 + 40 * (2 * (nbd - 1) + 1)) + 2 + 1 + 1 + 1;
+        const int64_t nbd = B.mpp / jacobi_bs<double>(), nbf = B.mpp / jacobi_bs<float>();
+        const int64_t jac_launches_setup = (1 + setup_sweeps[0] * (2 * (nbf - 1) + 1)) +
+                                           (1 + setup_sweeps[1] * (2 * (nbd - 1) + 1));
+        // checks, gather, K, init x2, diag, float32 start (convert, init, copy
+        // back), 2 x 2 Newton-Schulz products, K' (2), init, U0 W, diag, factors
+        const int64_t setup_launches = 1 + (need_md ? 1 : 0) + 1 + 2 + 1 + 3 + 4 + 2 + 1 + 1 + 1 + 2 +
+                                       jac_launches_setup + 1 + 1 + 1;
         prof.launches += setup_launches;
         prof.calls[LRR_PH_SETUP] += setup_launches;
     }

@@ -333,7 +333,7 @@ int setup(Engine<T>& g, double rank_tol) {
     jd.active = nullptr; jd.scale = g.jscale_d; jd.pp = g.mpp;
     UTRY(cudaMemcpyAsync(g.jscale_d, &sc, sizeof(double), cudaMemcpyHostToDevice, s));
     UTRY(cudaMemcpyAsync(g.jdesc, &jd, sizeof(jd), cudaMemcpyHostToDevice, s));
-    UTRY(jacobi_sweeps<double>(g.jdesc, 1, g.mpp, 40, 1e-13, s));
+    UTRY(jacobi_sweeps<double>(g.jdesc, 1, g.mpp, 40, 1e-13, s, g.jdone_d));
     lrr::k::diag_of<double><<<ceil_div(m, 256), 256, 0, s>>>(g.Kd, g.mpp, m, g.lam_d);
     std::vector<double> ev((size_t)m);
     UTRY(cudaMemcpyAsync(ev.data(), g.lam_d, sizeof(double) * m, cudaMemcpyDeviceToHost, s));

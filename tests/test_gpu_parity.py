@@ -259,10 +259,12 @@ def test_tensor_core_products_match_oracle(lib, precision):
     assert _rel(res.Z.cpu().numpy(), ref.Z) < 1e-5
 
 
-# ranks at clear gaps of the combined block spectrum (0.9996 | 0.9931 and
-# 0.62 | 2e-6 on this workload); the default k1 = 12 falls between 1.00187 and
-# 1.00169, where the truncation's subspace is not determined to float32 precision
-@pytest.mark.parametrize("rank", [24, 36])
+# ranks at clear gaps of the combined block spectrum (0.941 | 0.858 and
+# 0.62 | 2e-6 on this workload).  The truncated subspace moves by about the
+# blocks' float32 error over the relative gap at the cut: the default k1 = 12
+# falls between 1.00187 and 1.00169, and rank 24 (0.9996 | 0.9931, a 0.6 % gap)
+# measured 2.2e-5, so neither is determined to 1e-5 in float32
+@pytest.mark.parametrize("rank", [30, 36])
 def test_footnote_variant_matches_oracle(lib, rank):
     """Dictionary C_i per block (the footnote to eq. (2)), blocks solved as
     independent problems on concurrent streams, C step = truncated SVD of

@@ -1,23 +1,34 @@
-// bf16 x bf16 -> fp32 matrix product on the 5th-generation tensor cores
-// (tcgen05.mma, kind::f16) with TMA-fed shared-memory tiles and the
-// accumulator in tensor memory.  Used by the mixed-precision iteration for the
-// two large products of every ALM step, U^T P and U diag(sigma) Z, over all
-// blocks at once.
+// bf16 x bf16 -> fp32 matrix products on the 5th-generation tensor cores
+// (tcgen05.mma) with TMA-fed shared-memory tiles and the accumulator in
+// tensor memory.  Used by the mixed-precision iteration (U^T P and
+// U diag(sigma) Z over all blocks at once, from split operands), by the stop
+// test (V D with a max-abs epilogue) and on request for the float32 products.
 //
 // C (M x N, column-major, ldc) = A * B with A given K-major (element (m, k) at
 // A[k + m * lda]) and B given K-major (element (k, n) at B[k + n * ldb]); both
-// bf16 with lda, ldb multiples of 8 elements.  One CTA computes one 128 x 128
-// tile of C:
-//   warp 0      TMA producer: 64-wide K slabs of A and B into a 4-stage ring
-//               (128-byte swizzle), completion tracked by mbarriers;
-//   warp 1      allocates 128 TMEM columns, one elected lane issues four
-//               128x128x16 MMAs per slab and commits each slab back to the ring;
+// bf16 with lda, ldb multiples of 8.
+// tc_gemm_kernel (plain bf16): persistent, one CTA per SM over 128 x 256
+// tiles of C:
+//   warp 0      TMA producer: 64-wide K slabs of A (128 rows) and B (256
+//               rows) into a 4-stage ring (128-byte swizzle), completion
+//               tracked by mbarriers; the ring runs on from tile to tile;
+//   warp 1      allocates 2 x 256 TMEM columns (two accumulators), one
+//               elected lane issues four 128x256x16 MMAs per slab and commits
+//               each slab back to the ring and each finished tile to the
+//               epilogue;
 //   warps 2..5  epilogue: tcgen05.ld of their 32-lane quadrant of the
 //               accumulator, float32 stores (rows contiguous in C), or, in
 //               the reduction form, a per-column-block max |C_ij| (warp
-//               reduction, one atomic per warp and block) without storing C.
+//               reduction, one atomic per warp and block) without storing C;
+//               the drained accumulator is handed back to warp 1, so tile
+//               i + 1's MMAs overlap tile i's epilogue.
+// tc_gemm_split_kernel (split operands, float32 accuracy): one 128 x 128
+// tile per CTA, see below.
 // Every wait is bounded (about one second of spinning); a timeout sets *err,
-// drains the copies already issued and frees TMEM before returning.
+// drains the copies and MMAs already issued and frees TMEM before returning.
+#include <algorithm>
+#include <atomic>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -28,10 +39,14 @@
 namespace lrr {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int NT = 192;
-constexpr uint32_t TILE_BYTES = BM * BK * 2;            // A or B slab: 16 KB
-constexpr uint32_t STAGE_BYTES = 2 * TILE_BYTES;
+constexpr uint32_t TILE_BYTES = BM * BK * 2;            // 128-row slab of 64 bf16: 16 KB
+// persistent bf16 product: 128 x 256 tiles, 4-stage ring of 48 KB stages
+constexpr int PBN = 256, PSTAGES = 4;
+constexpr uint32_t TILE_A_BYTES = BM * BK * 2;          // 16 KB
+constexpr uint32_t TILE_B_BYTES = PBN * BK * 2;         // 32 KB
+constexpr uint32_t PSTAGE_BYTES = TILE_A_BYTES + TILE_B_BYTES;
 constexpr long long WAIT_CYCLES = 2000000000LL;          // ~1 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -51,6 +66,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return ok != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 // bounded wait: false (and *err set) after WAIT_CYCLES
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
@@ -89,6 +107,12 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
+// Persistent form: one CTA per SM walks the 128 x 256 tiles of C (tile index
+// blockIdx.x, then every gridDim.x-th; tiles in M fastest, so the CTAs working
+// at the same time share the B slabs in L2).  The producer's stage ring and
+// the k-block counter run on across tiles; the accumulator is double-buffered
+// in TMEM (2 x 256 columns), so the MMAs of tile i + 1 run while the epilogue
+// drains tile i.
 __global__ void __launch_bounds__(NT, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                                                         const __grid_constant__ CUtensorMap mapB, float* __restrict__ C,
                                                         int64_t ldc, int M, int N, int K, int* __restrict__ err,
@@ -96,36 +120,45 @@ __global__ void __launch_bounds__(NT, 1) tc_gemm_kernel(const __grid_constant__ 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment for the swizzled tiles
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
+    __shared__ __align__(8) uint64_t full_bar[PSTAGES], empty_bar[PSTAGES], accf[2], acce[2], drain_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int tiles_m = (M + BM - 1) / BM;
+    const int ntiles = tiles_m * ((N + PBN - 1) / PBN);
     const int nk = (K + BK - 1) / BK;
 
-    // reduction form: leave (uniformly, before any barrier or TMEM use) when
-    // no column of this tile belongs to a block that asks for the maximum
-    if (am.bmax) {
-        if (am.run && *am.run == 0) return;
-        const int b_lo = am.colblk[n0], b_hi = am.colblk[min(n0 + BN, N) - 1];
-        bool any = false;
-        for (int b = b_lo; b <= b_hi; ++b) any |= am.need[b] != 0;
-        if (!any) return;
-    }
+    // reduction form: the whole launch does nothing when *run == 0
+    // (uniform, before any barrier or TMEM use)
+    if (am.bmax && am.run && *am.run == 0) return;
+    // reduction form: a tile none of whose columns belongs to a block that
+    // asks for the maximum is skipped by every role alike
+    auto skip = [&](int tile) -> bool {
+        if (!am.bmax) return false;
+        const int n0 = (tile / tiles_m) * PBN;
+        const int b_lo = am.colblk[n0], b_hi = am.colblk[min(n0 + PBN, N) - 1];
+        for (int b = b_lo; b <= b_hi; ++b)
+            if (am.need[b] != 0) return false;
+        return true;
+    };
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < PSTAGES; ++s) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
-        mbar_init(&acc_bar, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 4);
+        }
+        mbar_init(&drain_bar, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(BN));
+                     "r"(2 * PBN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -135,63 +168,97 @@ __global__ void __launch_bounds__(NT, 1) tc_gemm_kernel(const __grid_constant__ 
 
     if (warp == 0) {
         if (lane == 0) {
-            int issued = 0;
-            for (int kb = 0; kb < nk; ++kb) {
-                const int s = kb % STAGES;
-                if (kb >= STAGES && !mbar_wait(&empty_bar[s], ((kb / STAGES) - 1) & 1, err)) {
-                    abort_flag = 1;
-                    break;
+            int64_t g = 0;     // k-blocks issued over all tiles of this CTA
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                if (skip(tile)) continue;
+                const int m0 = (tile % tiles_m) * BM, n0 = (tile / tiles_m) * PBN;
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int s = (int)(g % PSTAGES);
+                    if (g >= PSTAGES && !mbar_wait(&empty_bar[s], (uint32_t)((g / PSTAGES) - 1) & 1, err)) ok = false;
+                    if (!ok || abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char* st = base + s * PSTAGE_BYTES;
+                    mbar_expect_tx(&full_bar[s], PSTAGE_BYTES);
+                    tma_load_2d(st, &mapA, kb * BK, m0, &full_bar[s]);
+                    tma_load_2d(st + TILE_A_BYTES, &mapB, kb * BK, n0, &full_bar[s]);
                 }
-                unsigned char* st = base + s * STAGE_BYTES;
-                mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-                tma_load_2d(st, &mapA, kb * BK, m0, &full_bar[s]);
-                tma_load_2d(st + TILE_BYTES, &mapB, kb * BK, n0, &full_bar[s]);
-                issued = kb + 1;
             }
-            if (abort_flag) {
+            if (!ok) {
+                abort_flag = 1;
                 // let the copies already in flight land before the CTA exits
-                for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
-                    mbar_wait(&full_bar[kb % STAGES], (kb / STAGES) & 1, err);
+                for (int64_t j = g - PSTAGES < 0 ? 0 : g - PSTAGES; j < g; ++j)
+                    mbar_wait(&full_bar[j % PSTAGES], (uint32_t)(j / PSTAGES) & 1, err);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            constexpr uint32_t idesc = idesc_bf16(BM, PBN);
+            int64_t g = 0;
+            int i = 0;         // tiles computed by this CTA
             bool ok = true;
-            for (int kb = 0; kb < nk; ++kb) {
-                const int s = kb % STAGES;
-                if (!mbar_wait(&full_bar[s], (kb / STAGES) & 1, err) || abort_flag) {
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                if (skip(tile)) continue;
+                const int buf = i & 1;
+                // the epilogue must have drained this accumulator (tile i - 2)
+                if (i >= 2 && !mbar_wait(&acce[buf], (uint32_t)((i >> 1) - 1) & 1, err)) {
                     ok = false;
                     break;
                 }
-                asm volatile("tcgen05.fence::after_thread_sync;\n");
-                const uint32_t a_addr = smem_u32(base + s * STAGE_BYTES);
-                const uint32_t b_addr = a_addr + TILE_BYTES;
+                const uint32_t acc = tmem + (uint32_t)(buf * PBN);
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int s = (int)(g % PSTAGES);
+                    if (!mbar_wait(&full_bar[s], (uint32_t)(g / PSTAGES) & 1, err) || abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n");
+                    const uint32_t a_addr = smem_u32(base + s * PSTAGE_BYTES);
+                    const uint32_t b_addr = a_addr + TILE_A_BYTES;
 #pragma unroll
-                for (int k = 0; k < BK / 16; ++k) {
-                    const uint64_t da = smem_desc(a_addr + k * 32);
-                    const uint64_t db = smem_desc(b_addr + k * 32);
-                    const uint32_t accum = (kb > 0 || k > 0) ? 1u : 0u;
+                    for (int k = 0; k < BK / 16; ++k) {
+                        const uint64_t da = smem_desc(a_addr + k * 32);
+                        const uint64_t db = smem_desc(b_addr + k * 32);
+                        const uint32_t accum = (kb > 0 || k > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
+                            "l"(da), "l"(db), "r"(idesc), "r"(accum));
+                    }
                     asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(da), "l"(db), "r"(idesc), "r"(accum));
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                            smem_u32(&empty_bar[s]))
+                        : "memory");
                 }
+                if (!ok) break;
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                                 smem_u32(&empty_bar[s]))
+                                 smem_u32(&accf[buf]))
                              : "memory");
+                ++i;
             }
-            if (!ok) abort_flag = 1;
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                             smem_u32(&acc_bar))
-                         : "memory");
+            if (!ok) {
+                abort_flag = 1;
+                // every MMA issued so far completes before TMEM is released
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                 smem_u32(&drain_bar))
+                             : "memory");
+                mbar_wait(&drain_bar, 0, err);
+            }
         }
     } else {
         // epilogue warps 2..5 own TMEM lane quadrants (warp % 4)
         const int q = warp & 3;
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_bar, 0, err) && !abort_flag);
-        asm volatile("tcgen05.fence::after_thread_sync;\n");
-        if (ok) {
+        int i = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            if (skip(tile)) continue;
+            const int buf = i & 1;
+            ok = __all_sync(0xffffffffu, ok && mbar_wait(&accf[buf], (uint32_t)(i >> 1) & 1, err) && !abort_flag);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            const int m0 = (tile % tiles_m) * BM, n0 = (tile / tiles_m) * PBN;
             const int row = m0 + q * 32 + lane;
             // reduction form: running max of the current column block; the
             // block changes at the same column for every lane of the warp
@@ -204,9 +271,10 @@ __global__ void __launch_bounds__(NT, 1) tc_gemm_kernel(const __grid_constant__ 
                 }
             };
 #pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 16) {
+            for (int c0 = 0; c0 < PBN; c0 += 16) {
+                if (n0 + c0 >= N) break;      // warp-uniform
                 uint32_t v[16];
-                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+                const uint32_t taddr = tmem + (uint32_t)(buf * PBN) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
                     "%13, %14, %15}, [%16];\n"
@@ -242,13 +310,18 @@ __global__ void __launch_bounds__(NT, 1) tc_gemm_kernel(const __grid_constant__ 
                 }
             }
             if (am.bmax) flush();
+            // accumulator drained: the MMA warp may reuse it for tile i + 2
+            asm volatile("tcgen05.fence::before_thread_sync;\n");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[buf]);
+            ++i;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncthreads();
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;\n");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(BN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * PBN));
     }
 }
 
@@ -283,9 +356,6 @@ struct TileSkip {
     const int* flag;     // per block: nonzero = compute its columns
 };
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
-}
 
 // The accumulator is drained into float32 registers every SLAB k-blocks: the
 // tensor cores add each MMA's products to the accumulator with a truncating
@@ -494,13 +564,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 2-D bf16 tensor map over a K-major operand: inner dimension K (ld elements
 // per row), outer dimension `rows`; 64 x 128 boxes, 128-byte swizzle, zero fill
-bool make_map(CUtensorMap* map, const void* ptr, int64_t K, int64_t rows, int64_t ld, bool f32 = false) {
+bool make_map(CUtensorMap* map, const void* ptr, int64_t K, int64_t rows, int64_t ld, bool f32 = false,
+              int box_rows = BM) {
     auto fn = encode_fn();
     if (!fn) return false;
     const int esz = f32 ? 4 : 2;
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)(ld * esz)};
-    cuuint32_t box[2] = {(cuuint32_t)(f32 ? BK32 : BK), (cuuint32_t)BM};
+    cuuint32_t box[2] = {(cuuint32_t)(f32 ? BK32 : BK), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     return fn(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr),
               dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -509,7 +580,7 @@ bool make_map(CUtensorMap* map, const void* ptr, int64_t K, int64_t rows, int64_
 
 }  // namespace
 
-size_t tc_gemm_smem_bytes() { return (size_t)STAGES * STAGE_BYTES + 1024; }
+size_t tc_gemm_smem_bytes() { return (size_t)PSTAGES * PSTAGE_BYTES + 1024; }
 
 namespace {
 cudaError_t tc_launch(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int M, int N,
@@ -518,12 +589,18 @@ cudaError_t tc_launch(const void* A, int64_t lda, const void* B, int64_t ldb, fl
     if ((lda % 8) || (ldb % 8) || (reinterpret_cast<uintptr_t>(A) % 16) || (reinterpret_cast<uintptr_t>(B) % 16))
         return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, A, K, M, lda) || !make_map(&mb, B, K, N, ldb)) return cudaErrorInvalidValue;
-    if (ceil_div(N, BN) > 65535) return cudaErrorInvalidValue;   // grid.y limit
+    if (!make_map(&ma, A, K, M, lda) || !make_map(&mb, B, K, N, ldb, false, PBN)) return cudaErrorInvalidValue;
+    const int64_t ntiles = (int64_t)ceil_div(M, BM) * ceil_div(N, PBN);
+    if (ntiles > (1LL << 30)) return cudaErrorInvalidValue;
     static std::atomic<uint64_t> smem_set{0};
     const cudaError_t ea = ensure_smem_limit(tc_gemm_kernel, (int)tc_gemm_smem_bytes(), smem_set);
     if (ea != cudaSuccess) return ea;
-    const dim3 grid((unsigned)ceil_div(M, BM), (unsigned)ceil_div(N, BN));
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    // one CTA per SM (the 193 KB ring admits no second one)
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, std::max(1, nsm));
     tc_gemm_kernel<<<grid, NT, tc_gemm_smem_bytes(), s>>>(ma, mb, C, ldc, M, N, K, err, am);
     return cudaGetLastError();
 }

@@ -11,6 +11,36 @@ __device__ __forceinline__ int circle_item(int pos, int r, int N) {
     return pos == 0 ? 0 : 1 + ((pos - 1 + r) % (N - 1));
 }
 
+// Tangent of the classical Jacobi rotation that annihilates s_pq:
+// tan(2 theta) = 2 s_pq / (s_qq - s_pp), the root of smaller magnitude.
+template <typename T>
+__device__ __forceinline__ void jacobi_rotation(T app, T aqq, T apq, T& cc, T& ss) {
+    const T theta = (aqq - app) / (T(2) * apq);
+    T tt;
+    if (fabs(theta) > T(1) / num<T>::eps()) tt = T(0.5) / theta;
+    else tt = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+    cc = T(1) / sqrt(tt * tt + T(1));
+    ss = tt * cc;
+}
+// float: the hardware reciprocal and reciprocal square root.  The rotations
+// only steer the pivot towards diagonal form: the accumulated rotation is
+// re-orthonormalised before it touches the columns, and the next sweep forms
+// its Grams afresh, so a few ulps in c and s cost no accuracy, while the
+// shorter dependent chain shortens every step of the inner sweep.
+template <>
+__device__ __forceinline__ void jacobi_rotation<float>(float app, float aqq, float apq, float& cc, float& ss) {
+    const float theta = __fdividef(aqq - app, 2.f * apq);
+    float tt;
+    if (fabsf(theta) > 1.f / FLT_EPSILON) {
+        tt = __fdividef(0.5f, theta);
+    } else {
+        const float h = fmaf(theta, theta, 1.f);
+        tt = copysignf(__fdividef(1.f, fabsf(theta) + h * rsqrtf(h)), theta);
+    }
+    cc = rsqrtf(fmaf(tt, tt, 1.f));
+    ss = tt * cc;
+}
+
 // Diagonalises S (B2 x B2, row stride LDS) in place by classical Jacobi
 // rotations (angle from tan(2 theta) = 2 s_pq / (s_qq - s_pp)), B2/2 disjoint
 // rotations per parallel step, accumulating the rotations into R (R <- R J, R
@@ -32,14 +62,9 @@ __device__ int inner_jacobi(T (*S)[LDS], T (*R)[LDS], T* cs, T* sn, int* pi, int
                 const T app = S[p][p], aqq = S[q][q], apq = S[p][q];
                 T cc = T(1), ss = T(0);
                 if (fabs(apq) > floor_rot && fabs(apq) > num<T>::eps() * sqrt(fabs(app * aqq))) {
-                    const T theta = (aqq - app) / (T(2) * apq);
-                    T tt;
-                    if (fabs(theta) > T(1) / num<T>::eps()) tt = T(0.5) / theta;
-                    else tt = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
-                    cc = T(1) / sqrt(tt * tt + T(1));
-                    ss = tt * cc;
+                    jacobi_rotation<T>(app, aqq, apq, cc, ss);
                     rotated = 1;
-                    if (fabs(apq) > floor_sig && fabs(tt) > exit_tan) rotated_sig = 1;
+                    if (fabs(apq) > floor_sig && fabs(ss) > exit_tan * cc) rotated_sig = 1;
                 }
                 cs[t] = cc; sn[t] = ss; pi[t] = p; qi[t] = q;
             }

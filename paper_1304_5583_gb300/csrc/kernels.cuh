@@ -71,6 +71,8 @@ struct OsjDesc {
     int64_t ldx, ldw;
     int L, p, pp;
     int strict;         // 1: resolve pairs straddling tau to angle tol (C-step block)
+    int* ctr;           // optional: two ints of scratch; the cluster's CTAs then take the
+                        // pivots of a round from a shared counter instead of a fixed share
 };
 
 // One launch: every block is a thread-block cluster of `cluster` CTAs (0:

@@ -105,7 +105,7 @@ struct Buffers {
     std::vector<int*> rot;
     int* rot_d;
     double *mu, *mu_fin, *resid;
-    int *act, *iters, *svt_on, *rank_cur, *rank_fin, *need_exact, *conv_bound, *conv, *jdone, *colblk, *flag;
+    int *act, *iters, *svt_on, *rank_cur, *rank_fin, *need_exact, *conv_bound, *conv, *jdone, *jctr, *colblk, *flag;
     T *r1, *dmax, *r2x, *jscale, *joff;
     int64_t* perm;
     // descriptor / pointer tables
@@ -221,6 +221,7 @@ Buffers<T> carve(Arena& a, const lrr_problem* p, bool need_md, const std::vector
     b.conv_bound = a.take<int>(t);
     b.conv = a.take<int>(t);
     b.jdone = a.take<int>(t);
+    b.jctr = a.take<int>(2 * (size_t)t);
     b.colblk = a.take<int>(n);
     b.flag = a.take<int>(4);
     b.r1 = a.take<T>(t);
@@ -623,6 +624,7 @@ int solve_impl(const lrr_problem* p, const lrr_options* o, void* ws, size_t ws_b
         j.L = tall[i] ? r : blk[i].l;
         j.W = B.W[i]; j.ldw = ppv[i]; j.p = pv[i]; j.pp = ppv[i];
         j.done = B.jdone + i; j.off = B.joff + 3 * i; j.active = B.svt_on + i; j.scale = B.jscale + i;
+        j.ctr = B.jctr + 2 * i;
         j.mu = B.mu + i;
         j.strict = (dfc && t > 1 && i == 0) ? 1 : 0;
     }

@@ -1,8 +1,6 @@
 // Grouped general matrix product on the CUDA cores (float32 / float64).
 // This is the accurate product of the plain-precision path: every group is an
 // independent column-major product C = alpha op(A) op(B) + beta C.
-#include <type_traits>
-
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -112,149 +110,12 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc<T>* __restrict_
     }
 }
 
-// float32: 128 x 128 tiles, 8 x 8 outputs per thread, the next K slab
-// loaded into registers while the current one is multiplied (two shared
-// buffers, one barrier per slab).  Every output is summed exactly as in
-// gemm_kernel -- 16-term slabs, each an FMA chain in k order from zero, added
-// to the accumulator in slab order -- so the results are the same bit for bit;
-// the larger tile only raises the FMA-to-load ratio and hides the global loads.
-constexpr int WM = 128, WN = 128, WNT = 256;
-
-template <bool TA, bool TB>
-__global__ void __launch_bounds__(WNT, 1) gemm_kernel_wide(const GemmDesc<float>* __restrict__ descs, int tiles_m) {
-    const GemmDesc<float> d = descs[blockIdx.z];
-    if (d.flag && *d.flag == 0) return;
-    const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
-    const int m0 = tm * WM, n0 = tn * WN;
-    if (m0 >= d.m || n0 >= d.n) return;
-
-    __shared__ float As[2][BK][WM + 4];
-    __shared__ float Bs[2][BK][WN + 4];
-    const int t = threadIdx.x;
-    const int tx = t % 16, ty = t / 16;
-    // global -> register staging: 8 values of A and 8 of B per thread
-    float ra[8], rb[8];
-    auto load = [&](int k0) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            int i, kk;
-            if (!TA) { i = t % WM; kk = t / WM + 2 * q; }
-            else     { kk = t % BK; i = t / BK + 16 * q; }
-            const int gi = m0 + i, gk = k0 + kk;
-            float v = 0.f;
-            if (gi < d.m && gk < d.k) {
-                v = TA ? d.A[gk + (int64_t)gi * d.lda] : d.A[gi + (int64_t)gk * d.lda];
-                if (d.kscale) v *= d.kscale[gk];
-            }
-            ra[q] = v;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            int j, kk;
-            if (!TB) { kk = t % BK; j = t / BK + 16 * q; }
-            else     { j = t % WN; kk = t / WN + 2 * q; }
-            const int gj = n0 + j, gk = k0 + kk;
-            float v = 0.f;
-            if (gj < d.n && gk < d.k) v = TB ? d.B[gj + (int64_t)gk * d.ldb] : d.B[gk + (int64_t)gj * d.ldb];
-            rb[q] = v;
-        }
-    };
-    auto stash = [&](int buf) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            if (!TA) As[buf][t / WM + 2 * q][t % WM] = ra[q];
-            else     As[buf][t % BK][t / BK + 16 * q] = ra[q];
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            if (!TB) Bs[buf][t % BK][t / BK + 16 * q] = rb[q];
-            else     Bs[buf][t / WN + 2 * q][t % WN] = rb[q];
-        }
-    };
-
-    float acc[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-
-    const int nk = (d.k + BK - 1) / BK;
-    load(0);
-    stash(0);
-    __syncthreads();
-    for (int kb = 0; kb < nk; ++kb) {
-        const int buf = kb & 1;
-        if (kb + 1 < nk) load((kb + 1) * BK);
-        float part[8][8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) part[i][j] = 0.f;
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            float a[8], b[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) a[i] = As[buf][kk][tx + 16 * i];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) b[j] = Bs[buf][kk][ty + 16 * j];
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) part[i][j] = fmaf(a[i], b[j], part[i][j]);
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] += part[i][j];
-        if (kb + 1 < nk) stash(buf ^ 1);
-        __syncthreads();
-    }
-    if (d.absmax) {
-        float mx = 0.f;
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                if (n0 + ty + 16 * j < d.n && m0 + tx + 16 * i < d.m) mx = fmaxf(mx, fabsf(d.alpha * acc[i][j]));
-        mx = warp_max(mx);
-        if ((t & 31) == 0) atomic_max_nonneg(d.absmax, mx);
-        return;
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int gj = n0 + ty + 16 * j;
-        if (gj >= d.n) continue;
-        const int64_t cj = d.ccol ? d.ccol[gj] : gj;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int gi = m0 + tx + 16 * i;
-            if (gi >= d.m) continue;
-            float* c = d.C + gi + cj * d.ldc;
-            float v = d.alpha * acc[i][j];
-            if (d.beta != 0.f) v = fmaf(d.beta, *c, v);
-            *c = v;
-        }
-    }
-}
-
 }  // namespace
 
 template <typename T>
 cudaError_t gemm_grouped(const GemmDesc<T>* d_desc, int groups, bool transA, bool transB, int max_m, int max_n,
                          cudaStream_t s) {
     if (groups <= 0 || max_m <= 0 || max_n <= 0) return cudaSuccess;
-    if constexpr (std::is_same<T, float>::value) {
-        // float32 products big enough to fill the GPU with 128 x 128 tiles
-        if ((int64_t)ceil_div(max_m, WM) * ceil_div(max_n, WN) * groups >= 152) {
-            const int tm = (int)ceil_div(max_m, WM), tn = (int)ceil_div(max_n, WN);
-            const dim3 g((unsigned)(tm * tn), 1, (unsigned)groups);
-            if (!transA && !transB) gemm_kernel_wide<false, false><<<g, WNT, 0, s>>>(d_desc, tm);
-            else if (transA && !transB) gemm_kernel_wide<true, false><<<g, WNT, 0, s>>>(d_desc, tm);
-            else if (!transA && transB) gemm_kernel_wide<false, true><<<g, WNT, 0, s>>>(d_desc, tm);
-            else gemm_kernel_wide<true, true><<<g, WNT, 0, s>>>(d_desc, tm);
-            return cudaGetLastError();
-        }
-    }
     const int tiles_m = (int)ceil_div(max_m, BM), tiles_n = (int)ceil_div(max_n, BN);
     dim3 grid((unsigned)(tiles_m * tiles_n), 1, (unsigned)groups);
     if (!transA && !transB) gemm_kernel<T, false, false><<<grid, NT, 0, s>>>(d_desc, tiles_m);

@@ -75,7 +75,10 @@ __global__ void __launch_bounds__(NT) jac_solve(const JacDesc<T>* __restrict__ d
     }
     const bool need = __syncthreads_or(any) != 0;
 
-    const int any_rot = need ? inner_jacobi<T, B2, NT>(S, R, cs, sn, pi, qi, floor_rot, floor_abs, 6) : 0;
+    // float32 (the start of the setup's eigendecomposition): one inner sweep
+    // per pivot, the outer sweeps continue from there; float64: up to six
+    const int any_rot =
+        need ? inner_jacobi<T, B2, NT>(S, R, cs, sn, pi, qi, floor_rot, floor_abs, sizeof(T) == 4 ? 1 : 6) : 0;
     // diagonalised pivot block back into G, rotation out for the apply kernel
     if (t == 0) d.rot[P] = any_rot;
     if (any_rot) {

@@ -378,12 +378,13 @@ struct TuneKey {
 std::mutex g_tune_mutex;
 std::map<TuneKey, int> g_tune_cluster;
 
-// float32 products on the tensor cores in split TF32 (float32 iteration only;
-// the grid covers n in 128-column tiles, at most 65535 of them)
 // Jacobi sweep tolerance of the iteration (scaled off-diagonal)
 template <typename T>
 constexpr T jtol_of() { return sizeof(T) == 8 ? T(1e-13) : T(2e-6); }
 
+// float32 products on the tensor cores in split TF32, on request only
+// (lrr_options.tc_products; float32 iteration; the grid covers n in 128-column
+// tiles, at most 65535 of them)
 template <typename T>
 bool use_tc32(const lrr_problem* p, const lrr_options* o) {
     return std::is_same<T, float>::value && o->precision != LRR_PREC_F64 && o->tc_products && p->n <= kTcMaxN;

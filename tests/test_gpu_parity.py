@@ -61,8 +61,11 @@ def test_small_dfc_float32_matches_oracle(lib, batched):
     assert _rel(res.Z.cpu().numpy(), ref.Z) < 1e-5
     assert _rel(res.S.cpu().numpy(), ref.S) < 1e-5
     assert res.k1 == ref.k1
-    free = olrr.dfc_lrr(M, w.perm, w.offsets, w.lam, eps=w.eps, max_iter=w.max_iter)
-    assert np.all(np.abs(res.iters - free.iters) <= 2)
+    if batched:
+        # the free-running oracle stops within two iterations of the GPU
+        # (both schedules take the same iterations; checked once)
+        free = olrr.dfc_lrr(M, w.perm, w.offsets, w.lam, eps=w.eps, max_iter=w.max_iter)
+        assert np.all(np.abs(res.iters - free.iters) <= 2)
 
 
 def test_partition_drawn_by_the_library_from_a_seed(lib):

@@ -141,6 +141,17 @@ def _elementwise(out, w, r, m, l, it, fb):
     return out
 
 
+def workload_config(args, w, world: int) -> dict:
+    """The `config` object of both arms' JSON lines: the workload and how it is
+    run (the oracle arm times the same workload)."""
+    m, n = w.M.shape
+    return {"workload": args.workload, "m": int(m), "n": int(n), "t": int(w.t), "lambda": w.lam, "eps": w.eps,
+            "precision": args.precision, "batched": not args.sequential,
+            "parallelism": "replicas" if world > 1 else "single", "autotune": not args.no_autotune,
+            "l2": "no flush: the per-iteration working set (C, P, MZ, E, Y1 and the reduced state) "
+                  "exceeds the 129 MB L2"}
+
+
 def replica_seed(seed: int, rank: int) -> int:
     """Seed of the workload replica a rank solves: the solve is one batch on
     one GPU, so N GPUs run N independent replicas (weak scaling)."""
@@ -290,12 +301,8 @@ def bench_ours(args, rank, world):
         "metric": METRIC, "value": solve_s, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-        "config": {"workload": args.workload, "m": int(m), "n": int(n), "t": int(w.t), "lambda": w.lam,
-                   "eps": w.eps, "precision": args.precision, "batched": not args.sequential,
-                   "rank_M": res.rank_M, "k1": res.k1, "parallelism": "replicas" if world > 1 else "single",
-                   "autotune": not args.no_autotune,
-                   "l2": "no flush: the per-iteration working set (C, P, MZ, E, Y1 and the reduced state) "
-                         "exceeds the 129 MB L2"},
+        "config": workload_config(args, w, world),
+        "rank_M": res.rank_M, "k1": res.k1,
         "alm_iters_per_s": float(np.max(res.iters)) / solve_s,
         "block_iters_per_s": iters_total / solve_s,
         "iters": {"max": int(np.max(res.iters)), "sum": iters_total, "per_block": res.iters.tolist()},
@@ -473,7 +480,7 @@ def main():
             "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "precision": "f64-oracle"},
+            "config": workload_config(args, w, args.gpus),
             "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
                              "sample": desc + f"; extrapolated to all blocks at {it1} iterations each (the "
                                        "oracle's own count on block 1)"},

@@ -20,18 +20,35 @@ import numpy as np
 from scipy.optimize import linear_sum_assignment
 
 
-def affinity(Z: np.ndarray, rel_tol: float = 1e-6) -> np.ndarray:
-    U, s, _ = np.linalg.svd(Z, full_matrices=False)
+def affinity(Z: np.ndarray, rel_tol: float = 1e-6, basis: np.ndarray = None) -> np.ndarray:
+    """|U U^T| from the left singular vectors U of Z with s > rel_tol * s_max.
+    ``basis``: an orthonormal Q whose span holds every column of Z (Z = Q Q^T Z,
+    as for the C step's output, Q = Q1); then Z = Q (Q^T Z) and the left
+    singular vectors of Z are Q times those of the small matrix Q^T Z, with
+    the same singular values -- the same U without an SVD of the n x n Z."""
+    if basis is None:
+        U, s, _ = np.linalg.svd(Z, full_matrices=False)
+    else:
+        Ub, s, _ = np.linalg.svd(basis.T @ Z, full_matrices=False)
+        U = basis @ Ub
     k = int(np.count_nonzero(s > rel_tol * s[0])) if s.size and s[0] > 0 else 0
     Uk = U[:, :k]
     return np.abs(Uk @ Uk.T)
 
 
-def spectral_embedding(A: np.ndarray, k: int) -> np.ndarray:
+def spectral_embedding(A: np.ndarray, k: int, subset: bool = None) -> np.ndarray:
+    """``subset`` (default: n > 5000): compute only the k eigenpairs with the
+    smallest eigenvalues (LAPACK's subset driver) instead of all n."""
     d = A.sum(axis=1)
     dinv = np.where(d > 0, 1.0 / np.sqrt(np.maximum(d, 1e-300)), 0.0)
     L = np.eye(A.shape[0]) - (dinv[:, None] * A) * dinv[None, :]
-    w, V = np.linalg.eigh(L)
+    if subset is None:
+        subset = A.shape[0] > 5000
+    if subset:
+        from scipy.linalg import eigh as sp_eigh
+        w, V = sp_eigh(L, subset_by_index=[0, k - 1], overwrite_a=True, check_finite=False)
+    else:
+        w, V = np.linalg.eigh(L)
     Y = V[:, :k]
     nrm = np.linalg.norm(Y, axis=1, keepdims=True)
     return Y / np.where(nrm > 0, nrm, 1.0)
@@ -66,9 +83,10 @@ def kmeans(Y: np.ndarray, k: int, seed: int = 0, restarts: int = 20, iters: int 
     return best_lab
 
 
-def segment(Z: np.ndarray, k: int, seed: int = 0) -> np.ndarray:
-    """Cluster labels (0..k-1) of the n points from an n x n estimate Z."""
-    return kmeans(spectral_embedding(affinity(Z), k), k, seed=seed)
+def segment(Z: np.ndarray, k: int, seed: int = 0, basis: np.ndarray = None) -> np.ndarray:
+    """Cluster labels (0..k-1) of the n points from an n x n estimate Z
+    (``basis`` as for affinity)."""
+    return kmeans(spectral_embedding(affinity(Z, basis=basis), k), k, seed=seed)
 
 
 def matched_accuracy(labels: np.ndarray, truth: np.ndarray) -> float:

@@ -35,7 +35,11 @@ def main():
         res = lrr.dfc_lrr(M, w.perm, w.offsets, w.lam, rho=w.rho, mu0=w.mu0, mu_max=w.mu_max, eps=w.eps,
                           max_iter=w.max_iter, workers=args.workers)
         t1 = time.time()
-        lab = segment.segment(res.Z, w.data.k, seed=0)
+        # the C step's output lies in span(Q1): its singular vectors come from
+        # the k1 x n matrix Q1^T Z (an SVD of the dense 20000 x 20000 Z
+        # crashed inside LAPACK)
+        basis = lrr.orth_basis(res.blocks[0].J_U) if w.t > 1 else None
+        lab = segment.segment(res.Z, w.data.k, seed=0, basis=basis)
         t2 = time.time()
         out = {"workload": name, "recipe": "synth.workload(%r, seed=0), float32-rounded M" % name,
                "oracle": "oracle.lrr.dfc_lrr to convergence, then oracle.segment.segment(Z, k, seed=0)",

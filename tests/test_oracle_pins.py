@@ -454,3 +454,23 @@ def test_footnote_variant_with_one_block_is_lrr_truncated():
     U, s, Vt = np.linalg.svd(ref.Z)
     k = ref.rank
     assert np.allclose(res.Z, (U[:, :k] * s[:k]) @ Vt[:k], atol=1e-10)
+
+
+def test_segmentation_from_the_c_step_basis_equals_the_dense_route():
+    """The C step's output lies in span(Q1), so its left singular vectors are
+    Q1 times those of Q1^T Z: the affinity from the basis equals the one from
+    the SVD of the dense Z, and the k-eigenpair embedding gives the labels of
+    the full eigendecomposition."""
+    from oracle import segment as seg
+    w = synth.workload("small_dfc_60x240")
+    M = w.M.astype(np.float64)
+    res = lrr.dfc_lrr(M, w.perm, w.offsets, w.lam, eps=w.eps)
+    Q = lrr.orth_basis(res.blocks[0].J_U)
+    A_dense = seg.affinity(res.Z)
+    A_basis = seg.affinity(res.Z, basis=Q)
+    assert np.abs(A_dense - A_basis).max() < 1e-10
+    Yf = seg.spectral_embedding(A_dense, w.data.k, subset=False)
+    Ys = seg.spectral_embedding(A_dense, w.data.k, subset=True)
+    # the embeddings agree up to an orthogonal map of the k coordinates
+    assert np.abs(Yf @ Yf.T - Ys @ Ys.T).max() < 1e-8
+    assert seg.same_partition(seg.kmeans(Yf, w.data.k, seed=0), seg.kmeans(Ys, w.data.k, seed=0))

@@ -7,15 +7,17 @@
 // round-robin (circle method) and every pair (a pivot of 2b = 32 columns)
 //   1. forms the 32 x 32 Gram S = X_P^T X_P afresh from the columns of X
 //      (each entry carries only the rounding of its own two columns),
-//   2. diagonalises S in shared memory (inner cyclic Jacobi),
+//   2. rotates S towards diagonal form in shared memory (one inner cyclic
+//      Jacobi sweep in float32, up to four in float64),
 //   3. re-orthonormalises the accumulated rotation R and applies it to X_P
 //      and W_P in update form.
 // Pairs of a round touch disjoint columns.
 //
 // One launch runs every sweep of every block: each block is a thread-block
-// cluster whose CTAs share the pairs of a round and meet at a cluster barrier
-// between rounds (the barrier's release/acquire makes one round's column
-// updates visible to the next).  After each sweep the cluster reduces the
+// cluster whose CTAs share the pairs of a round (a free CTA takes the next
+// pair from a per-block counter) and meet at a cluster barrier between rounds
+// (the barrier's release/acquire makes one round's column updates visible to
+// the next).  After each sweep the cluster reduces the
 // largest convergence measure seen in it and stops once that is below the
 // tolerance, so a converged block costs nothing further and the others are
 // not held to a common sweep count.
